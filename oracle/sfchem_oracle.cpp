@@ -1,0 +1,774 @@
+// sfchem_oracle.cpp -- plain FP64 CPU oracle for the SFUMATO# thermochemical
+// update (arXiv 2604.21438, Sec. 2.2.8 and Appendices A-C).
+//
+// TEST INFRASTRUCTURE ONLY: loaded by the tests, by the smoke check and by
+// the benchmark's CPU-baseline leg, never by the product path.  It shares no
+// code, header, table or constant with the CUDA library; every constant below
+// is written out here on its own.
+//
+// Style: slow and literal.  Derivatives of the chemistry rates and of the
+// heating/cooling functions are taken with forward-mode dual numbers (exact,
+// no finite differences); the dust / IR / gas-grain rows are written with the
+// coefficients printed in Appendix C (Eqs. ap_eq:Td2, the IR row and
+// ap_eq:Tg_2 with beta_d, beta_IR, gamma_d, zeta).  A 5x5 system is solved by
+// textbook Gaussian elimination with partial pivoting.
+//
+// Readings of passages the paper leaves open are marked "reading:"; the
+// stand-ins for physics the paper only cites ("see the reference") are marked
+// "stand-in:".  Stand-in physics is parity unpinned against nature: it is
+// pinned only through the closed forms and invariants of the tests.
+
+#include "sfchem_oracle.h"
+
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <algorithm>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// ---------------------------------------------------------------- constants
+const double kB = 1.380649e-16;        // erg/K
+const double mH = 1.67262192e-24;      // g, mass of the hydrogen nucleus (App. C)
+const double eV = 1.602176634e-12;     // erg
+const double c_light = 2.99792458e10;  // cm/s
+const double c_red = 1.0e-4 * c_light; // reduced light speed (Sec. 2.1)
+const double a_rad = 7.565733250e-15;  // erg cm^-3 K^-4
+const double T_CMB = 2.725;            // K; reading: z = 0
+const double y_He = 0.0833;            // reading: He per H nucleus
+const double R_g = 5.83e-8;            // App. C
+const double T_high = 1000.0;          // App. C
+const double T_low = 75.0;             // App. C
+const double C_d_unit = 1.0e4;         // erg g^-1 K^-1 (Sec. 2.2.8): C_d = cd_factor * 1e4
+const double INF = std::numeric_limits<double>::infinity();
+
+// stand-in constants (physics cited but not printed by the paper)
+const double sigma_EUV = 6.3e-18;   // cm^2, H photoionization cross-section at threshold
+const double k_LW = 3.3e-11;        // s^-1 per Habing unit, unshielded H2 photodissociation
+const double N_sh0 = 1.0e14;        // cm^-2, self-shielding onset
+const double sh_pow = 0.75;         // self-shielding power law
+const double zeta_CR = 1.0e-17;     // s^-1, cosmic-ray ionization rate per H
+const double E_PI = 2.0 * eV;       // heat per photoionization
+const double E_PD = 0.4 * eV;       // heat per H2 photodissociation
+const double PE_eps = 0.03;         // photoelectric efficiency
+const double x_C = 1.4e-4, TC_star = 91.2, A_C = 2.3e-6, g_C = 2.0, ncr_C = 2.3e-6 / 8.0e-10;
+const double x_O = 3.2e-4, TO_star = 228.0, A_O = 8.9e-5, g_O = 0.6, ncr_O = 8.9e-5 / 5.0e-10;
+const double kap0 = 0.1, kap_T0 = 10.0, kap_Tc = 200.0; // kappa_d^0(T) = kap0 (T/T0)^2 below Tc
+const double sigma_dUV = 1.0e-21;   // cm^2 per H, dust UV cross-section
+const double u_Habing = 5.29e-14;   // erg cm^-3 per G0
+const double hnu_EUV = 18.0 * eV;   // mean EUV photon energy
+
+// --------------------------------------------------------------- dual numbers
+// Forward-mode dual number over the four variables the chemistry and the gas
+// heating/cooling depend on: (y_H2, y_e, T_g, T_d).
+const int NV = 4;
+struct Dual {
+  double v;
+  double g[NV];
+};
+Dual cst(double v) { Dual r; r.v = v; for (int i = 0; i < NV; ++i) r.g[i] = 0.0; return r; }
+Dual var(double v, int k) { Dual r = cst(v); r.g[k] = 1.0; return r; }
+Dual operator+(const Dual &a, const Dual &b) { Dual r; r.v = a.v + b.v; for (int i = 0; i < NV; ++i) r.g[i] = a.g[i] + b.g[i]; return r; }
+Dual operator-(const Dual &a, const Dual &b) { Dual r; r.v = a.v - b.v; for (int i = 0; i < NV; ++i) r.g[i] = a.g[i] - b.g[i]; return r; }
+Dual operator*(const Dual &a, const Dual &b) { Dual r; r.v = a.v * b.v; for (int i = 0; i < NV; ++i) r.g[i] = a.g[i] * b.v + a.v * b.g[i]; return r; }
+Dual operator/(const Dual &a, const Dual &b) { Dual r; r.v = a.v / b.v; for (int i = 0; i < NV; ++i) r.g[i] = (a.g[i] * b.v - a.v * b.g[i]) / (b.v * b.v); return r; }
+Dual operator+(const Dual &a, double s) { Dual r = a; r.v += s; return r; }
+Dual operator+(double s, const Dual &a) { return a + s; }
+Dual operator-(const Dual &a, double s) { Dual r = a; r.v -= s; return r; }
+Dual operator-(double s, const Dual &a) { Dual r; r.v = s - a.v; for (int i = 0; i < NV; ++i) r.g[i] = -a.g[i]; return r; }
+Dual operator-(const Dual &a) { return 0.0 - a; }
+Dual operator*(const Dual &a, double s) { Dual r; r.v = a.v * s; for (int i = 0; i < NV; ++i) r.g[i] = a.g[i] * s; return r; }
+Dual operator*(double s, const Dual &a) { return a * s; }
+Dual operator/(const Dual &a, double s) { return a * (1.0 / s); }
+Dual operator/(double s, const Dual &a) { return cst(s) / a; }
+Dual dexp(const Dual &a) { double e = std::exp(a.v); Dual r; r.v = e; for (int i = 0; i < NV; ++i) r.g[i] = e * a.g[i]; return r; }
+Dual dlog(const Dual &a) { Dual r; r.v = std::log(a.v); for (int i = 0; i < NV; ++i) r.g[i] = a.g[i] / a.v; return r; }
+Dual dsqrt(const Dual &a) { double s = std::sqrt(a.v); Dual r; r.v = s; for (int i = 0; i < NV; ++i) r.g[i] = a.g[i] / (2.0 * s); return r; }
+Dual dpow(const Dual &a, double p) { double v = std::pow(a.v, p); Dual r; r.v = v; double d = p * std::pow(a.v, p - 1.0); for (int i = 0; i < NV; ++i) r.g[i] = d * a.g[i]; return r; }
+Dual dlog10(const Dual &a) { return dlog(a) / std::log(10.0); }
+
+// ------------------------------------------------------------------ helpers
+bool bit(uint32_t m, uint32_t b) { return (m & b) != 0; }
+bool rbit(const oracle_config &c, int i) { return (c.reaction_mask >> i) & 1u; }
+
+struct CellIn {      // per-cell inputs that the step does not evolve
+  double n;          // n_H
+  double G0, nEUV, NH2;
+  double Cd;         // C_d
+  double fd;         // f_d = Z / Zsun
+  double rho;        // gas density
+};
+
+CellIn make_cell(double n, double G0, double nEUV, double NH2, double cd_factor, const oracle_config &c) {
+  CellIn ci;
+  ci.n = n; ci.G0 = G0; ci.nEUV = nEUV; ci.NH2 = NH2;
+  ci.Cd = cd_factor * C_d_unit;
+  ci.fd = c.Z;
+  ci.rho = (1.0 + 4.0 * y_He) * mH * n;
+  return ci;
+}
+
+// --------------------------------------------------- Table 3: rate coefficients
+// k[i] is k_H<i>; T = T_g and Td = T_d as dual numbers (Table 3, Appendix A).
+void rates(const Dual &T, const Dual &Td, const CellIn &ci, const oracle_config &c, Dual k[12]) {
+  // H0: collisional ionization, polynomial in ln T_g(eV); reading: T(eV) = T/11604.5
+  {
+    Dual x = dlog(T / 11604.5);
+    const double a[9] = {-32.71396786, 13.536556, -5.73932875, 1.563154998, -0.2877056,
+                         3.48255977e-2, -2.63197617e-3, 1.11954395e-4, -2.03914985e-6};
+    Dual p = cst(0.0), xp = cst(1.0);
+    for (int i = 0; i < 9; ++i) { p = p + a[i] * xp; xp = xp * x; }
+    k[0] = dexp(p);
+  }
+  // H1: radiative recombination
+  k[1] = 2.753e-14 * dpow(315614.0 / T, 1.5) * dpow(1.0 + dpow(115188.0 / T, 0.407), -2.242);
+  // H2: H- formation
+  k[2] = 1.4e-18 * dpow(T, 0.928) * dexp(-T / 16200.0);
+  // H3: associative detachment
+  k[3] = 1.35e-9 * (dpow(T, 0.098493) + 0.32852 * dpow(T, 0.5561) + 2.771e-7 * dpow(T, 2.1826)) /
+         (1.0 + 6.191e-3 * dpow(T, 1.0461) + 8.9712e-11 * dpow(T, 3.0424) + 3.2576e-14 * dpow(T, 3.7741));
+  // H5: three-body formation; H6 = H5 / 8
+  Dual k5 = 6e-32 * dpow(T, -0.25) + 2e-31 * dpow(T, -0.5);
+  k[5] = k5;
+  k[6] = k5 / 8.0;
+  // H7: k_high^(1-a) k_low^a, written through logarithms (the same number)
+  Dual k7;
+  {
+    Dual L = dlog10(T / 1.0e4);
+    Dual log10_ncr = 4.845 - 1.3 * L + 1.62 * L * L;
+    Dual ncr = dexp(std::log(10.0) * log10_ncr);
+    Dual a = 1.0 / (1.0 + ci.n / ncr);
+    Dual ln_klow = std::log(1.18e-10) - 6.95e4 / T;
+    Dual ln_khigh = std::log(8.125e-8) - 0.5 * dlog(T) - 5.2e4 / T + dlog(1.0 - dexp(-6000.0 / T));
+    k7 = dexp((1.0 - a) * ln_khigh + a * ln_klow);
+  }
+  k[7] = k7;
+  // H4: stand-in -- the collisional dissociation by H is given the same
+  // functional form and coefficients as H7 (the paper prints only a citation)
+  k[4] = k7;
+  // H8: H2 formation on grains
+  {
+    Dual fa = 1.0 / (1.0 + dexp(7.5e2 * (1.0 / 75.0 - 1.0 / Td)));
+    k[8] = 6.0e-17 * dsqrt(T / 300.0) * fa * ci.fd /
+           (1.0 + 4.0e-2 * dsqrt(T + Td) + 2.0e-3 * T + 8.0e-6 * T * T);
+  }
+  // H9: stand-in photoionization rate c * sigma * n_EUV
+  k[9] = cst(c_light * sigma_EUV * ci.nEUV);
+  // H10: stand-in photodissociation k_LW G0 f_sh(N_H2), power-law self-shielding
+  {
+    double fsh = ci.NH2 > N_sh0 ? std::pow(ci.NH2 / N_sh0, -sh_pow) : 1.0;
+    k[10] = cst(k_LW * ci.G0 * fsh);
+  }
+  // H11: stand-in cosmic-ray ionization
+  k[11] = cst(zeta_CR);
+  for (int i = 0; i < 12; ++i)
+    if (!rbit(c, i)) k[i] = cst(0.0);
+}
+
+// ------------------------------------------- reaction rates R_i (Eq. eq_chemq)
+// With H- in equilibrium between its formation (H2) and destruction (H3),
+// the H- channel forms H2 at k_H2 n y_H y_e and returns the electron.
+void chem_rates(const Dual &yH2, const Dual &ye, const Dual k[12], const CellIn &ci,
+                const oracle_config &c, Dual &RH2, Dual &Re) {
+  double n = ci.n;
+  Dual yH = 1.0 - 2.0 * yH2 - ye;   // H-nuclei conservation, y_H+ = y_e (Sec. 2.2.8)
+  Dual yHp = ye;
+  Dual via_Hm = (rbit(c, 2) && rbit(c, 3)) ? k[2] * n * yH * ye : cst(0.0);
+  RH2 = via_Hm + k[5] * n * n * yH * yH * yH + k[6] * n * n * yH * yH * yH2 + k[8] * n * yH -
+        k[4] * n * yH * yH2 - k[7] * n * yH2 * yH2 - k[10] * yH2;
+  Re = k[0] * n * yH * ye + k[9] * yH + k[11] * yH - k[1] * n * yHp * ye;
+}
+
+// ---------------- Table 4: heating minus cooling (volumetric), excluding gas-grain
+Dual line2(const Dual &T, double n, double x, double Tstar, double A, double g, double ncr, double fd) {
+  Dual e = g * dexp(-Tstar / T);
+  return x * fd * n * (kB * Tstar) * A * e / (1.0 + e + ncr / n);
+}
+
+Dual gas_heat_cool(const Dual &yH2, const Dual &ye, const Dual &T, const Dual k[12],
+                   const CellIn &ci, const oracle_config &c) {
+  double n = ci.n, n2 = n * n;
+  uint32_t m = c.process_mask;
+  Dual yH = 1.0 - 2.0 * yH2 - ye, yHp = ye;
+  Dual net = cst(0.0);
+  if (bit(m, ORACLE_P_G1_H2FORM)) {
+    // reading: the third term is formation on grains, (0.2 + 4.2 f) eV per H2 formed by H8
+    Dual Dn = 1.6 * yH * dexp(-(400.0 / T) * (400.0 / T)) + 1.4 * yH2 * dexp(-12000.0 / (T + 1200.0));
+    Dual f = n * Dn / (n * Dn + 1.0e6 / dsqrt(T));   // (1 + n_cr/n)^-1
+    Dual via_Hm = (rbit(c, 2) && rbit(c, 3)) ? k[2] * n2 * yH * ye : cst(0.0);
+    net = net + eV * (3.73 * f * via_Hm + 4.48 * f * k[5] * n2 * n * yH * yH * yH +
+                      (0.2 + 4.2 * f) * k[8] * n2 * yH);
+  }
+  if (bit(m, ORACLE_P_G2_PHOTOION)) net = net + E_PI * k[9] * n * yH;
+  if (bit(m, ORACLE_P_G3_PHOTODISS)) net = net + E_PD * k[10] * n * yH2;
+  if (bit(m, ORACLE_P_G4_PHOTOELEC)) net = net + cst(1.0e-24 * PE_eps * ci.G0 * n * ci.fd);
+  if (bit(m, ORACLE_P_L5_HION)) net = net - 13.6 * eV * k[0] * n2 * yH * ye;
+  if (bit(m, ORACLE_P_L6_H2DISS)) net = net - 4.48 * eV * (k[4] * n2 * yH2 * yH + k[7] * n2 * yH2 * yH2);
+  if (bit(m, ORACLE_P_L7_HREC)) {
+    Dual L = dlog10(T);
+    Dual p = -25.87 + 0.4958 * L - 0.1052 * L * L + 0.04264 * L * L * L - 9.165e-3 * L * L * L * L +
+             5.491e-4 * L * L * L * L * L;
+    net = net - dexp(std::log(10.0) * p) * n2 * yHp * ye;
+  }
+  if (bit(m, ORACLE_P_L8_HMFB)) net = net - kB * T * k[2] * n2 * yH * ye;
+  // reading: H excitation is collisions of electrons with neutral H
+  if (bit(m, ORACLE_P_L9_HEXC))
+    net = net - 7.50e-19 / (1.0 + dsqrt(T / 1.0e5)) * dexp(-118348.0 / T) * n2 * ye * yH;
+  if (bit(m, ORACLE_P_L10_HEPEXC))
+    net = net - 5.54e-17 * dpow(T, -0.397) / (1.0 + dsqrt(T / 1.0e5)) * dexp(-473638.0 / T) * n2 * ye * y_He;
+  if (bit(m, ORACLE_P_L11_FF)) {
+    Dual gff = T.v < 3.2e5 ? 0.79464 + 0.1243 * dlog10(T) : 2.13164 - 0.1240 * dlog10(T);
+    net = net - 1.426e-27 * dsqrt(T) * gff * n2 * yHp * ye;
+  }
+  if (bit(m, ORACLE_P_L12_COMPTON))
+    net = net - 1.017e-37 * std::pow(T_CMB, 4) * (T - T_CMB) * n * ye;
+  if (bit(m, ORACLE_P_L13_LINE)) {
+    // stand-in: two-level C+ (158 um) and O (63 um) with fixed abundances scaled by f_d
+    net = net - line2(T, n, x_C, TC_star, A_C, g_C, ncr_C, ci.fd) - line2(T, n, x_O, TO_star, A_O, g_O, ncr_O, ci.fd);
+  }
+  return net;
+}
+
+// ----------------------------------------------------- Appendix C dust terms
+double kappa(double T) { return T < kap_Tc ? kap0 * (T / kap_T0) * (T / kap_T0) : kap0 * (kap_Tc / kap_T0) * (kap_Tc / kap_T0); }
+double dkappa(double T) { return T < kap_Tc ? 2.0 * kap0 * T / (kap_T0 * kap_T0) : 0.0; }
+
+struct DustTerms {
+  double T_IR;         // a T_IR^4 = (c~/c) E_IR
+  double emit;         // kappa(T_d) a c T_d^4
+  double irabs;        // kappa(T_IR) c~ E_IR
+  double EUV;          // dust absorption of EUV+FUV
+  double G;            // R_g n_H sqrt(T_g / T_high), zero when gas-grain is off
+  double gam;          // gamma_d (Eq. ap_eq:gamma_d)
+  double zeta;         // Eq. ap_eq:zeta
+  double beta_d;       // Eq. ap_eq:beta_d
+  double beta_IR;      // Eq. ap_eq:beta_IR
+  double D;            // C_d dT_d/dt  (Eq. ap_eq:dust_temp)
+  double I;            // dE_IR/dt     (Eq. ap_eq:Eir)
+  double Qgg;          // de_th/dt from gas-grain transfer (Eq. ap_eq:Tg)
+};
+
+DustTerms dust_terms(double Tg, double Td, double E, const CellIn &ci, const oracle_config &c) {
+  DustTerms d;
+  uint32_t m = c.process_mask;
+  bool on_emit = bit(m, ORACLE_P_DUST_EMIT), on_irabs = bit(m, ORACLE_P_DUST_IRABS);
+  bool on_uv = bit(m, ORACLE_P_DUST_UV), on_gg = bit(m, ORACLE_P_GASGRAIN);
+  d.T_IR = std::pow((c_red / c_light) * E / a_rad, 0.25);
+  d.emit = on_emit ? kappa(Td) * a_rad * c_light * std::pow(Td, 4) : 0.0;
+  d.irabs = on_irabs ? kappa(d.T_IR) * c_red * E : 0.0;
+  // stand-in: E_UV = c kappa_UV (u_FUV + u_EUV), kappa_UV per gas mass
+  double kap_UV = sigma_dUV / ((1.0 + 4.0 * y_He) * mH);
+  d.EUV = on_uv ? c_light * kap_UV * (ci.G0 * u_Habing + ci.nEUV * hnu_EUV) : 0.0;
+  d.G = on_gg ? R_g * ci.n * std::sqrt(Tg / T_high) : 0.0;
+  d.gam = 1.0 - 0.8 * std::exp(-T_low / Tg);
+  d.zeta = d.gam / 2.0 * (Td / Tg - 1.0) + (d.gam - 1.0) * T_low / Tg * (Td / Tg - 1.0) - d.gam;
+  d.beta_d = on_emit ? 4.0 * kappa(Td) + dkappa(Td) * Td : 0.0;
+  d.beta_IR = on_irabs ? kappa(d.T_IR) + dkappa(d.T_IR) * d.T_IR / 4.0 : 0.0;
+  d.D = d.irabs + d.EUV - d.emit - d.G * d.gam * (Td - Tg);
+  d.I = ci.rho * ci.fd * (d.emit - d.irabs);
+  d.Qgg = ci.fd * d.G * d.gam * (Td - Tg);
+  return d;
+}
+
+// --------------------------------------------------------------- gas state
+struct GasState { double ntot, mu, alpha_g, P; };
+GasState gas_state(double yH2, double ye, double Tg, const CellIn &ci, const oracle_config &c) {
+  GasState s;
+  double yH = 1.0 - 2.0 * yH2 - ye;
+  s.ntot = ci.n * (yH + yH2 + ye + ye + y_He);                       // H, H2, H+, e, He
+  s.mu = ci.rho / (s.ntot * mH);
+  s.alpha_g = kB / ((c.gamma_ad - 1.0) * s.mu * mH);                  // Eq. ap_eq:alpha_g
+  s.P = s.ntot * kB * Tg;
+  return s;
+}
+
+// ------------------------------------------------ one LI substep's system
+struct System {
+  double F[5];      // right-hand sides (R_H2, R_e, q + Q_gg, D, I)
+  double J[5][5];   // dF/du (exact)
+  double M[5];      // 1, 1, alpha_g, C_d, 1
+  double ts[3];     // dt_dust, dt_chem, dt_energy
+  double aux[5];    // rho, alpha_g, E_UV, P, Gamma - Lambda (volumetric, incl. gas-grain)
+  DustTerms d;
+};
+
+double E_floor_of() { return (c_light / c_red) * a_rad * std::pow(T_CMB, 4); }
+
+double ratio_ts(double x, double rate) { return rate != 0.0 ? std::fabs(x) / std::fabs(rate) : INF; }
+
+System build_system(const double u[5], const CellIn &ci, const oracle_config &c) {
+  System s;
+  std::memset(&s, 0, sizeof(s));
+  uint32_t fl = c.flags;
+  Dual yH2 = var(u[0], 0), ye = var(u[1], 1), T = var(u[2], 2), Td = var(u[3], 3);
+  Dual k[12];
+  rates(T, Td, ci, c, k);
+  Dual RH2, Re;
+  chem_rates(yH2, ye, k, ci, c, RH2, Re);
+  Dual net = gas_heat_cool(yH2, ye, T, k, ci, c);
+  Dual q = net / ci.rho;                                  // per unit mass
+  DustTerms d = dust_terms(u[2], u[3], u[4], ci, c);
+  GasState gs = gas_state(u[0], u[1], u[2], ci, c);
+  s.d = d;
+  // chemistry rows (Eq. eq_deq): exact partial derivatives
+  s.F[0] = RH2.v;
+  s.F[1] = Re.v;
+  for (int j = 0; j < 4; ++j) { s.J[0][j] = RH2.g[j]; s.J[1][j] = Re.g[j]; }
+  // gas row: (Gamma' - Lambda')/rho plus the gas-grain term of Eq. ap_eq:Tg
+  s.F[2] = q.v + d.Qgg;
+  for (int j = 0; j < 4; ++j) s.J[2][j] = q.g[j];
+  s.J[2][2] += ci.fd * d.G * d.zeta;       // d/dT_g of Q_gg (the zeta term of Eq. ap_eq:Tg_2)
+  s.J[2][3] += ci.fd * d.G * d.gam;        // d/dT_d of Q_gg
+  // dust row (Eq. ap_eq:Td2) and IR row, coefficients of Appendix C
+  double acTd3 = a_rad * c_light * std::pow(u[3], 3);
+  s.F[3] = d.D;
+  s.J[3][3] = -(d.G * d.gam + acTd3 * d.beta_d);
+  s.J[3][4] = c_red * d.beta_IR;
+  s.J[3][2] = -d.G * d.zeta;
+  s.F[4] = d.I;
+  s.J[4][3] = ci.rho * acTd3 * ci.fd * d.beta_d;
+  s.J[4][4] = -ci.rho * c_red * ci.fd * d.beta_IR;
+  // reading: the split variant keeps only the blocks that eq_deq and App. C print
+  if (bit(fl, ORACLE_F_SPLIT)) {
+    s.J[0][2] = s.J[0][3] = s.J[1][2] = s.J[1][3] = 0.0;
+    s.J[2][0] = s.J[2][1] = 0.0;
+    s.J[2][3] -= q.g[3];
+  }
+  double Cd = ci.Cd;
+  s.M[0] = 1.0; s.M[1] = 1.0; s.M[2] = gs.alpha_g; s.M[3] = Cd; s.M[4] = 1.0;
+  // timescales (Eqs. timescale_of_dust, timescale_chemi, timescale_energy)
+  double tdust = INF;
+  if (!bit(fl, ORACLE_F_FREEZE_TD)) tdust = std::min(tdust, ratio_ts(u[3], d.D / Cd));
+  if (!bit(fl, ORACLE_F_FREEZE_TG)) tdust = std::min(tdust, ratio_ts(u[2], d.Qgg / gs.alpha_g));
+  if (!bit(fl, ORACLE_F_FREEZE_EIR)) tdust = std::min(tdust, ratio_ts(u[4], d.I));
+  double tchem = INF;
+  // reading: the abundance in Eq. timescale_chemi is floored at y_floor
+  if (!bit(fl, ORACLE_F_FREEZE_YH2)) tchem = std::min(tchem, ratio_ts(std::max(u[0], c.y_floor), RH2.v));
+  if (!bit(fl, ORACLE_F_FREEZE_YE)) tchem = std::min(tchem, ratio_ts(std::max(u[1], c.y_floor), Re.v));
+  double GmL = ci.rho * (q.v + d.Qgg);
+  double tener = INF;
+  if (!bit(fl, ORACLE_F_FREEZE_TG)) tener = GmL != 0.0 ? gs.P / ((c.gamma_ad - 1.0) * std::fabs(GmL)) : INF;
+  s.ts[0] = tdust; s.ts[1] = tchem; s.ts[2] = tener;
+  s.aux[0] = ci.rho; s.aux[1] = gs.alpha_g; s.aux[2] = d.EUV; s.aux[3] = gs.P; s.aux[4] = GmL;
+  return s;
+}
+
+// (M - dt J) du = dt F, with frozen variables' rows replaced by du_j = 0
+void assemble(const System &s, double dt, const oracle_config &c, double A[25], double b[5]) {
+  for (int r = 0; r < 5; ++r) {
+    for (int j = 0; j < 5; ++j) A[r * 5 + j] = (r == j ? s.M[r] : 0.0) - dt * s.J[r][j];
+    b[r] = dt * s.F[r];
+  }
+  const uint32_t fr[5] = {ORACLE_F_FREEZE_YH2, ORACLE_F_FREEZE_YE, ORACLE_F_FREEZE_TG,
+                          ORACLE_F_FREEZE_TD, ORACLE_F_FREEZE_EIR};
+  for (int r = 0; r < 5; ++r)
+    if (bit(c.flags, fr[r])) {
+      for (int j = 0; j < 5; ++j) A[r * 5 + j] = (r == j) ? 1.0 : 0.0;
+      b[r] = 0.0;
+    }
+}
+
+// Gaussian elimination, partial pivoting (largest |a| in the column, lowest
+// row index on ties), back substitution.
+int solve_n(int N, const double *Ain, const double *bin, double *x) {
+  double A[25], b[5];
+  std::memcpy(A, Ain, sizeof(double) * N * N);
+  std::memcpy(b, bin, sizeof(double) * N);
+  for (int col = 0; col < N; ++col) {
+    int p = col;
+    for (int r = col + 1; r < N; ++r)
+      if (std::fabs(A[r * N + col]) > std::fabs(A[p * N + col])) p = r;
+    if (A[p * N + col] == 0.0) return -1;
+    if (p != col) {
+      for (int j = 0; j < N; ++j) std::swap(A[p * N + j], A[col * N + j]);
+      std::swap(b[p], b[col]);
+    }
+    for (int r = col + 1; r < N; ++r) {
+      double f = A[r * N + col] / A[col * N + col];
+      for (int j = col; j < N; ++j) A[r * N + j] -= f * A[col * N + j];
+      b[r] -= f * b[col];
+    }
+  }
+  for (int r = N - 1; r >= 0; --r) {
+    double s = b[r];
+    for (int j = r + 1; j < N; ++j) s -= A[r * N + j] * x[j];
+    x[r] = s / A[r * N + r];
+  }
+  return 0;
+}
+
+// abundance and floor projection after an update (reading of the positivity
+// rules, which the paper leaves open)
+void project(double u[5]) {
+  u[1] = std::min(std::max(u[1], 0.0), 1.0);
+  u[0] = std::min(std::max(u[0], 0.0), (1.0 - u[1]) / 2.0);
+  u[2] = std::max(u[2], T_CMB);
+  u[3] = std::max(u[3], T_CMB);
+  u[4] = std::max(u[4], E_floor_of());
+}
+
+// reading: a Newton correction (dT_d, dE_IR) of the tight-coupling iteration
+// is scaled by one factor lam <= 1 so that T_d changes by at most a factor 2
+// and E_IR (proportional to T_IR^4) by at most a factor 16 per iteration.
+double damp_factor(double Td, double E, double dTd, double dE) {
+  double lam = 1.0;
+  if (Td + dTd > 2.0 * Td) lam = std::min(lam, Td / dTd);
+  if (Td + dTd < 0.5 * Td) lam = std::min(lam, -0.5 * Td / dTd);
+  if (E + dE > 16.0 * E) lam = std::min(lam, 15.0 * E / dE);
+  if (E + dE < E / 16.0) lam = std::min(lam, -(15.0 / 16.0) * E / dE);
+  return lam;
+}
+
+// Backward-Euler Newton iteration on the dust and IR rows at fixed T_g and
+// chemistry (the tight-coupling iteration of Sec. 2.2.8; the NR solver's
+// group (ii)).  u holds the current iterate, u0 the step's start state.
+// Returns the iteration count, negative if the limit was reached.
+int newton_dust(double u[5], const double u0[5], double dt, const CellIn &ci, const oracle_config &c,
+                double tol, int limit) {
+  bool frTd = bit(c.flags, ORACLE_F_FREEZE_TD), frE = bit(c.flags, ORACLE_F_FREEZE_EIR);
+  if (frTd && frE) return 0;
+  for (int it = 1; it <= limit; ++it) {
+    DustTerms d = dust_terms(u[2], u[3], u[4], ci, c);
+    double acTd3 = a_rad * c_light * std::pow(u[3], 3);
+    double G4 = ci.Cd * (u[3] - u0[3]) - dt * d.D;
+    double G5 = (u[4] - u0[4]) - dt * d.I;
+    double J[4] = {ci.Cd + dt * (d.G * d.gam + acTd3 * d.beta_d), -dt * c_red * d.beta_IR,
+                   -dt * ci.rho * acTd3 * ci.fd * d.beta_d, 1.0 + dt * ci.rho * c_red * ci.fd * d.beta_IR};
+    double rhs[2] = {-G4, -G5};
+    if (frTd) { J[0] = 1.0; J[1] = 0.0; rhs[0] = 0.0; }
+    if (frE) { J[2] = 0.0; J[3] = 1.0; rhs[1] = 0.0; }
+    double del[2];
+    if (solve_n(2, J, rhs, del) != 0) return -it;
+    double lam = damp_factor(u[3], u[4], del[0], del[1]);
+    u[3] += lam * del[0];
+    u[4] += lam * del[1];
+    project(u);
+    if (lam == 1.0 && std::fabs(del[0]) <= tol * u[3] && std::fabs(del[1]) <= tol * u[4]) return it;
+  }
+  return -limit;
+}
+
+bool valid_input(double n, double Tg, double Td, double E, double yH2, double ye, double G0,
+                 double nEUV, double NH2, double dt) {
+  double v[10] = {n, Tg, Td, E, yH2, ye, G0, nEUV, NH2, dt};
+  for (double x : v) if (!std::isfinite(x)) return false;
+  if (!(n > 0.0 && Tg > 0.0 && Td > 0.0 && E >= 0.0 && yH2 >= 0.0 && ye >= 0.0 && ye <= 1.0)) return false;
+  if (!(2.0 * yH2 + ye <= 1.0 + 1e-9)) return false;
+  if (!(G0 >= 0.0 && nEUV >= 0.0 && NH2 >= 0.0 && dt >= 0.0)) return false;
+  return true;
+}
+
+// The LI step of one cell over dt_h (Sec. 2.2.8 "Time stepping").
+// rec (optional) receives 7 doubles per substep.
+struct LIOut { int nsub; int nitr; uint8_t status; };
+
+LIOut li_cell(double u[5], const CellIn &ci, double dt_h, const oracle_config &c, int max_rec, double *rec) {
+  LIOut o = {0, 0, 0};
+  project(u);
+  if (dt_h == 0.0) return o;
+  // mode: estimated number of subcycles from the start state (reading: once per call)
+  System s0 = build_system(u, ci, c);
+  bool tight = !(dt_h < (double)c.n_cyc * c.f_chem * s0.ts[0]);
+  if (tight) o.status |= ORACLE_ST_TIGHT;
+  double t = 0.0;
+  while (true) {
+    System s = build_system(u, ci, c);
+    double tmin = std::min(s.ts[1], s.ts[2]);
+    if (!tight) tmin = std::min(tmin, s.ts[0]);
+    double dtc = c.f_chem * tmin;                     // Eq. timestep_subcycle
+    double rem = dt_h - t;
+    bool last = false;
+    double dts;
+    // reading: the last substep is truncated to the time left, and a sliver
+    // below 1e-12 dt_hydro is merged into the substep before it
+    if (dtc >= rem || rem - dtc <= 1e-12 * dt_h) { dts = rem; last = true; }
+    else dts = dtc;
+    if (!(dts > 0.0) || !std::isfinite(dts)) { o.status |= ORACLE_ST_BADSTEP; break; }
+    double A[25], b[5], du[5], u0[5];
+    assemble(s, dts, c, A, b);
+    std::memcpy(u0, u, sizeof(u0));
+    if (solve_n(5, A, b, du) != 0) { o.status |= ORACLE_ST_BADSTEP; break; }
+    for (int j = 0; j < 5; ++j) u[j] += du[j];
+    project(u);
+    if (tight) {
+      // reading: the Newton iteration starts from the LI update of (T_d, E_IR)
+      // limited like a Newton correction (factor 2 in T_d, 16 in E_IR)
+      double lam = damp_factor(u0[3], u0[4], u[3] - u0[3], u[4] - u0[4]);
+      if (lam < 1.0) {
+        u[3] = u0[3] + lam * (u[3] - u0[3]);
+        u[4] = u0[4] + lam * (u[4] - u0[4]);
+        project(u);
+      }
+      int it = newton_dust(u, u0, dts, ci, c, c.nr_tol, c.nr_itr_limit);
+      if (it < 0) { o.status |= ORACLE_ST_NOCONV; it = -it; }
+      o.nitr += it;
+    }
+    t = last ? dt_h : t + dts;
+    if (rec && o.nsub < max_rec) {
+      double *r = rec + 7 * o.nsub;
+      r[0] = t; r[1] = dts; r[2] = u[0]; r[3] = u[1]; r[4] = u[2]; r[5] = u[3]; r[6] = u[4];
+    }
+    o.nsub++;
+    if (last) break;
+    if (o.nsub >= c.n_sub_max) { o.status |= ORACLE_ST_CAP; break; }
+  }
+  return o;
+}
+
+// ------------------------------------------------------- NR reference (B.E.)
+// Group (iii): species at fixed (T_g, T_d).  Returns iterations, <0 on failure.
+int newton_species(double u[5], const double u0[5], double dt, const CellIn &ci, const oracle_config &c,
+                   double tol, int limit) {
+  bool fr0 = bit(c.flags, ORACLE_F_FREEZE_YH2), fr1 = bit(c.flags, ORACLE_F_FREEZE_YE);
+  if (fr0 && fr1) return 0;
+  for (int it = 1; it <= limit; ++it) {
+    Dual yH2 = var(u[0], 0), ye = var(u[1], 1), T = cst(u[2]), Td = cst(u[3]);
+    Dual k[12];
+    rates(T, Td, ci, c, k);
+    Dual RH2, Re;
+    chem_rates(yH2, ye, k, ci, c, RH2, Re);
+    double G[2] = {u[0] - u0[0] - dt * RH2.v, u[1] - u0[1] - dt * Re.v};
+    double J[4] = {1.0 - dt * RH2.g[0], -dt * RH2.g[1], -dt * Re.g[0], 1.0 - dt * Re.g[1]};
+    double rhs[2] = {-G[0], -G[1]};
+    if (fr0) { J[0] = 1.0; J[1] = 0.0; rhs[0] = 0.0; }
+    if (fr1) { J[2] = 0.0; J[3] = 1.0; rhs[1] = 0.0; }
+    double del[2];
+    if (solve_n(2, J, rhs, del) != 0) return -it;
+    u[0] += del[0];
+    u[1] += del[1];
+    project(u);
+    if (std::fabs(del[0]) <= tol * std::max(u[0], c.y_floor) &&
+        std::fabs(del[1]) <= tol * std::max(u[1], c.y_floor)) return it;
+  }
+  return -limit;
+}
+
+// Inner solves at a trial T_g, then the gas-energy residual
+// g(T_g) = alpha_g^t (T_g - T_g^t) - dt [ (Gamma'-Lambda')/rho + Q_gg ].
+bool nr_inner(double Tg, const double u0[5], double dt, const CellIn &ci, const oracle_config &c,
+              double tol, int limit, double uo[5], double &g) {
+  std::memcpy(uo, u0, sizeof(double) * 5);
+  uo[2] = Tg;
+  if (newton_dust(uo, u0, dt, ci, c, tol, limit) < 0) return false;
+  if (newton_species(uo, u0, dt, ci, c, tol, limit) < 0) return false;
+  Dual yH2 = cst(uo[0]), ye = cst(uo[1]), T = cst(uo[2]), Td = cst(uo[3]);
+  Dual k[12];
+  rates(T, Td, ci, c, k);
+  Dual net = gas_heat_cool(yH2, ye, T, k, ci, c);
+  DustTerms d = dust_terms(uo[2], uo[3], uo[4], ci, c);
+  GasState gs0 = gas_state(u0[0], u0[1], u0[2], ci, c);
+  g = gs0.alpha_g * (Tg - u0[2]) - dt * (net.v / ci.rho + d.Qgg);
+  return true;
+}
+
+// One backward-Euler step by nested Newton-Raphson; returns outer iterations
+// (>0) on convergence, <=0 on failure.
+int nr_be_step(double u[5], double dt, const CellIn &ci, const oracle_config &c) {
+  double u0[5];
+  std::memcpy(u0, u, sizeof(u0));
+  int limit = c.nr_itr_limit;
+  double uo[5], g;
+  if (bit(c.flags, ORACLE_F_FREEZE_TG)) {
+    if (!nr_inner(u0[2], u0, dt, ci, c, c.nr_tol, limit, uo, g)) return 0;
+    std::memcpy(u, uo, sizeof(uo));
+    return 1;
+  }
+  double Tg = u0[2];
+  for (int it = 1; it <= limit; ++it) {
+    // convergence criterion relaxed to 1e-3 after N_itr,limit / 2 iterations
+    double tol = (it > limit / 2) ? 1e-3 : c.nr_tol;
+    double h = 1e-4 * Tg;   // reading: central-difference step relative to T_g
+    double gp, gm;
+    double up[5], um[5];
+    if (!nr_inner(Tg, u0, dt, ci, c, tol, limit, uo, g)) return 0;
+    if (!nr_inner(Tg + h, u0, dt, ci, c, tol, limit, up, gp)) return 0;
+    if (!nr_inner(Tg - h, u0, dt, ci, c, tol, limit, um, gm)) return 0;
+    double dg = (gp - gm) / (2.0 * h);
+    if (dg == 0.0 || !std::isfinite(dg)) return 0;
+    double Tn = std::max(Tg - g / dg, T_CMB);
+    bool conv = std::fabs(Tn - Tg) <= tol * Tn;
+    Tg = Tn;
+    if (conv) {
+      if (!nr_inner(Tg, u0, dt, ci, c, tol, limit, uo, g)) return 0;
+      std::memcpy(u, uo, sizeof(uo));
+      return it;
+    }
+  }
+  return 0;
+}
+
+// Sec. 2.2.8: dt_hydro first; on failure dt_sub = (dt_hydro - t_sub) / 2^i
+// with i = 1 initially, i-1 after a success and i+1 after a failure.
+LIOut nr_cell(double u[5], const CellIn &ci, double dt_h, const oracle_config &c) {
+  LIOut o = {0, 0, 0};
+  project(u);
+  double t = 0.0;
+  int i = 0;
+  int tries = 0;
+  while (t < dt_h) {
+    double dts = (dt_h - t) / std::pow(2.0, i);
+    double uu[5];
+    std::memcpy(uu, u, sizeof(uu));
+    int it = nr_be_step(uu, dts, ci, c);
+    ++tries;
+    if (it > 0) {
+      std::memcpy(u, uu, sizeof(uu));
+      t = (i == 0) ? dt_h : t + dts;
+      o.nsub++;
+      o.nitr += it;
+      i = std::max(i - 1, 0);
+    } else {
+      i++;
+      if (i > 60 || tries > c.n_sub_max) { o.status |= ORACLE_ST_NOCONV; break; }
+    }
+  }
+  return o;
+}
+
+oracle_config checked(const oracle_config *cfg) {
+  oracle_config c;
+  if (cfg) c = *cfg; else oracle_default_config(&c);
+  return c;
+}
+
+}  // namespace
+
+extern "C" {
+
+void oracle_default_config(oracle_config *c) {
+  c->f_chem = 0.03;
+  c->n_cyc = 300;
+  c->n_sub_max = 100000;
+  c->Z = 1.0;
+  c->gamma_ad = 5.0 / 3.0;
+  c->y_floor = 1e-8;
+  c->reaction_mask = 0xFFFu;
+  c->process_mask = 0x1FFFFu;
+  c->flags = 0u;
+  c->nr_itr_limit = 20;
+  c->nr_tol = 1e-5;
+}
+
+int oracle_li_cells(int64_t n, const double *n_H, double *T_g, double *T_d, double *E_IR,
+                    double *y_H2, double *y_e, double *y_H, double *y_Hp, double *y_Hm,
+                    uint8_t *status, int32_t *n_sub, int32_t *n_itr, const double *G0,
+                    const double *n_EUV, const double *N_H2, const double *dt, double cd_factor,
+                    const oracle_config *cfg, int n_threads) {
+  if (n < 0 || !n_H || !T_g || !T_d || !E_IR || !y_H2 || !y_e || !G0 || !n_EUV || !N_H2 || !dt) return -1;
+  if (!(cd_factor > 0.0)) return -1;
+  oracle_config c = checked(cfg);
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    LIOut o = {0, 0, 0};
+    double u[5] = {y_H2[i], y_e[i], T_g[i], T_d[i], E_IR[i]};
+    if (!valid_input(n_H[i], T_g[i], T_d[i], E_IR[i], y_H2[i], y_e[i], G0[i], n_EUV[i], N_H2[i], dt[i])) {
+      o.status = ORACLE_ST_BADINPUT;
+    } else {
+      CellIn ci = make_cell(n_H[i], G0[i], n_EUV[i], N_H2[i], cd_factor, c);
+      o = li_cell(u, ci, dt[i], c, 0, nullptr);
+      y_H2[i] = u[0]; y_e[i] = u[1]; T_g[i] = u[2]; T_d[i] = u[3]; E_IR[i] = u[4];
+    }
+    bool ok = !(o.status & ORACLE_ST_BADINPUT);
+    if (y_H) y_H[i] = ok ? 1.0 - 2.0 * y_H2[i] - y_e[i] : NAN;
+    if (y_Hp) y_Hp[i] = ok ? y_e[i] : NAN;
+    if (y_Hm) {
+      if (ok) {
+        oracle_config ca = c;
+        ca.reaction_mask = 0xFFFu;
+        CellIn ci = make_cell(n_H[i], G0[i], n_EUV[i], N_H2[i], cd_factor, ca);
+        Dual k[12];
+        rates(cst(T_g[i]), cst(T_d[i]), ci, ca, k);
+        y_Hm[i] = k[2].v * y_e[i] / k[3].v;   // reading: H- balance of reactions H2 and H3
+      } else {
+        y_Hm[i] = NAN;
+      }
+    }
+    if (status) status[i] = o.status;
+    if (n_sub) n_sub[i] = o.nsub;
+    if (n_itr) n_itr[i] = o.nitr;
+  }
+  return 0;
+}
+
+int oracle_li_trace(double n_H, double T_g, double T_d, double E_IR, double y_H2, double y_e,
+                    double G0, double n_EUV, double N_H2, double dt, double cd_factor,
+                    const oracle_config *cfg, int max_rec, double *rec, uint8_t *status) {
+  oracle_config c = checked(cfg);
+  if (!valid_input(n_H, T_g, T_d, E_IR, y_H2, y_e, G0, n_EUV, N_H2, dt) || !(cd_factor > 0.0)) {
+    if (status) *status = ORACLE_ST_BADINPUT;
+    return 0;
+  }
+  CellIn ci = make_cell(n_H, G0, n_EUV, N_H2, cd_factor, c);
+  double u[5] = {y_H2, y_e, T_g, T_d, E_IR};
+  LIOut o = li_cell(u, ci, dt, c, max_rec, rec);
+  if (status) *status = o.status;
+  return o.nsub;
+}
+
+int oracle_nr_cells(int64_t n, const double *n_H, double *T_g, double *T_d, double *E_IR,
+                    double *y_H2, double *y_e, uint8_t *status, int32_t *n_sub, int32_t *n_itr,
+                    const double *G0, const double *n_EUV, const double *N_H2, const double *dt,
+                    double cd_factor, const oracle_config *cfg, int n_threads) {
+  if (n < 0 || !n_H || !T_g || !T_d || !E_IR || !y_H2 || !y_e || !G0 || !n_EUV || !N_H2 || !dt) return -1;
+  if (!(cd_factor > 0.0)) return -1;
+  oracle_config c = checked(cfg);
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    LIOut o = {0, 0, 0};
+    if (!valid_input(n_H[i], T_g[i], T_d[i], E_IR[i], y_H2[i], y_e[i], G0[i], n_EUV[i], N_H2[i], dt[i])) {
+      o.status = ORACLE_ST_BADINPUT;
+    } else {
+      CellIn ci = make_cell(n_H[i], G0[i], n_EUV[i], N_H2[i], cd_factor, c);
+      double u[5] = {y_H2[i], y_e[i], T_g[i], T_d[i], E_IR[i]};
+      o = nr_cell(u, ci, dt[i], c);
+      y_H2[i] = u[0]; y_e[i] = u[1]; T_g[i] = u[2]; T_d[i] = u[3]; E_IR[i] = u[4];
+    }
+    if (status) status[i] = o.status;
+    if (n_sub) n_sub[i] = o.nsub;
+    if (n_itr) n_itr[i] = o.nitr;
+  }
+  return 0;
+}
+
+void oracle_rates(double T_g, double T_d, double n_H, double G0, double n_EUV, double N_H2,
+                  const oracle_config *cfg, double k[12]) {
+  oracle_config c = checked(cfg);
+  CellIn ci = make_cell(n_H, G0, n_EUV, N_H2, 1.0, c);
+  Dual kd[12];
+  rates(cst(T_g), cst(T_d), ci, c, kd);
+  for (int i = 0; i < 12; ++i) k[i] = kd[i].v;
+}
+
+void oracle_system(double n_H, const double u[5], double G0, double n_EUV, double N_H2, double dt,
+                   double cd_factor, const oracle_config *cfg, double A[25], double b[5], double F[5],
+                   double Mdiag[5], double ts[3], double aux[5]) {
+  oracle_config c = checked(cfg);
+  CellIn ci = make_cell(n_H, G0, n_EUV, N_H2, cd_factor, c);
+  System s = build_system(u, ci, c);
+  assemble(s, dt, c, A, b);
+  for (int i = 0; i < 5; ++i) { F[i] = s.F[i]; Mdiag[i] = s.M[i]; aux[i] = s.aux[i]; }
+  for (int i = 0; i < 3; ++i) ts[i] = s.ts[i];
+}
+
+void oracle_rhs(double n_H, const double u[5], double G0, double n_EUV, double N_H2, double cd_factor,
+                const oracle_config *cfg, double dudt[5]) {
+  oracle_config c = checked(cfg);
+  CellIn ci = make_cell(n_H, G0, n_EUV, N_H2, cd_factor, c);
+  System s = build_system(u, ci, c);
+  const uint32_t fr[5] = {ORACLE_F_FREEZE_YH2, ORACLE_F_FREEZE_YE, ORACLE_F_FREEZE_TG,
+                          ORACLE_F_FREEZE_TD, ORACLE_F_FREEZE_EIR};
+  for (int i = 0; i < 5; ++i) dudt[i] = bit(c.flags, fr[i]) ? 0.0 : s.F[i] / s.M[i];
+}
+
+int oracle_solve5(const double A[25], const double b[5], double x[5]) { return solve_n(5, A, b, x); }
+
+}  // extern "C"
