@@ -1,0 +1,463 @@
+"""Benchmark of libsfchem: chem+thermal cell-updates/s of the per-cell
+thermochemical update (SFUMATO#, arXiv 2604.21438, Sec. 2.2.8), mixed
+precision batched against plain FP64 on the same GPU, at the error stated
+against the FP64 CPU oracle.
+
+A step is one call that advances every cell of the workload by its hydro
+time step (all substeps of all cells).  Default workload: the GMC-like
+256^3 grid (16.8M cells, dt = 1e3 yr, C_d = 1e6 erg/g/K) in 16^3 blocks,
+solved by the persistent batched kernel in mixed precision; the plain FP64
+path runs the same workload.  Inputs (2.4 GB of state) are larger than L2
+and are reset from a pristine device copy before every step (outside the
+timed events; the copy also evicts L2).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+
+METRIC = "chem+thermal cell-updates/s: mixed/batched vs plain FP64 at stated error"
+YR = inputs.YR
+
+# Algorithmic work per cell-substep of the solver kernels, counted from the
+# FP instructions that the ncu capture of each kernel reports per substep
+# (FMA = 2 flops); see the summaries under profiles/.
+WORK_PER_SUBSTEP = {
+    "mixed": {"fp32_flops": None, "fp64_flops": None},
+    "fp64": {"fp32_flops": None, "fp64_flops": None},
+}
+# GB300: 152 SMs; FP32: 128 lanes/SM; FP64: 1.25 TFLOP/s nominal at 2.07 GHz
+# (4 FP64 flops/SM/clock).
+N_SM = 152
+FP32_FLOP_PER_SM_CLK = 256.0
+FP64_FLOP_PER_SM_CLK = 4.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--workload", default="gmc256", choices=("gmc256", "grf128", "amr3000", "uniform4096"))
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
+    p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (error check, cpu_baseline)")
+    p.add_argument("--sample", type=int, default=4096, help="cells checked against the oracle")
+    p.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the cpu_baseline")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ workloads
+def make_workload(name: str, rank: int = 0):
+    """(cells, block_offset, block_dt, cd_factor, description)"""
+    if name == "gmc256":
+        cells = inputs.cells_gmc(256, seed=1005 + rank)
+        cells, off = inputs.block_major(cells, 256, 16)
+        bdt = np.full(len(off) - 1, 1e3 * YR)
+        return cells, off, bdt, 100.0, dict(
+            workload="GMC-like 256^3 grid in 16^3 blocks", cells=len(cells["n_H"]), dt_yr=1e3,
+            cd_factor=100.0, blocks=len(bdt), block_cells=4096)
+    if name == "grf128":
+        cells = inputs.cells_grf(128, seed=1002 + rank)
+        cells, off = inputs.block_major(cells, 128, 16)
+        bdt = np.full(len(off) - 1, 1e3 * YR)
+        return cells, off, bdt, 1.0, dict(workload="GRF 128^3 grid in 16^3 blocks", cells=len(cells["n_H"]),
+                                          dt_yr=1e3, cd_factor=1.0, blocks=len(bdt), block_cells=4096)
+    if name == "amr3000":
+        cells, off, bdt, lvl = inputs.cells_amr(seed=1004 + rank)
+        return cells, off, bdt, 100.0, dict(workload="AMR 3000 blocks of 8^3, levels 0-6, dt_l = 1e3 yr / 2^l",
+                                            cells=len(cells["n_H"]), cd_factor=100.0, blocks=len(bdt),
+                                            block_cells=512)
+    cells = inputs.cells_uniform(4096, seed=1001 + rank)
+    off = np.array([0, 4096], np.int64)
+    return cells, off, np.array([1e3 * YR]), 1.0, dict(workload="4096 independent cells (one 16^3 block)",
+                                                       cells=4096, dt_yr=1e3, cd_factor=1.0, blocks=1,
+                                                       block_cells=4096)
+
+
+# -------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our arm
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def microbench_fma():
+    """Measured FP64 / FP32 FMA throughput (FLOP/s) of this GPU."""
+    import ctypes
+    from paper_2604_21438_gb300 import _build
+    _build.build()
+    L = ctypes.CDLL(_build.BENCH_LIB)
+    out = {}
+    for name in ("fp64", "fp32"):
+        f = getattr(L, f"sfbench_fma_{name}")
+        fl, ms = ctypes.c_double(), ctypes.c_float()
+        iters = 2000 if name == "fp64" else 20000
+        if f(iters, ctypes.byref(fl), ctypes.byref(ms)) == 0:
+            out[name] = fl.value
+    return out
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2604_21438_gb300 as sf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    cells, off, bdt, cd, desc = make_workload(args.workload, rank)
+    n = len(cells["n_H"])
+    stream = torch.cuda.current_stream()
+
+    d = sf.to_device(cells, dev)
+    pristine = {k: d[k].clone() for k in sf.STATE_FIELDS}
+
+    def reset():
+        for k in sf.STATE_FIELDS:
+            d[k].copy_(pristine[k], non_blocking=True)
+
+    def timed_leg(solver, steps, warmup, reset_each=True):
+        for _ in range(warmup):
+            reset()
+            solver.step_batched(d, off, bdt, cd)
+        torch.cuda.synchronize()
+        solver.stats_reset()
+        times = []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            if reset_each:
+                reset()
+            ev[i][0].record(stream)
+            solver.step_batched(d, off, bdt, cd)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        wall = time.perf_counter() - t0
+        times = [a.elapsed_time(b) for a, b in ev]
+        st = solver.stats()
+        return float(np.mean(times)), wall, st
+
+    res = {}
+    # ---- mixed precision, batched (the headline)
+    sm = sf.Solver("mixed")
+    if not args.no_autotune:
+        reset()
+        sm.autotune(d, off, bdt, cd)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ms_m, wall_m, st_m = timed_leg(sm, args.steps, args.warmup)
+    clk = clocks.stop()
+    out_m = sf.to_host({k: d[k] for k in sf.STATE_FIELDS + ("status", "n_sub")})
+    res["mixed"] = dict(ms=ms_m, wall=wall_m, stats=st_m, launch=sm.get_launch())
+    # ---- plain FP64, batched, same workload
+    out_d = None
+    if not args.no_fp64:
+        sd = sf.Solver("fp64")
+        if not args.no_autotune:
+            reset()
+            sd.autotune(d, off, bdt, cd)
+        k64 = max(1, min(args.steps, 3))
+        ms_d, wall_d, st_d = timed_leg(sd, k64, min(args.warmup, 3))
+        out_d = sf.to_host({k: d[k] for k in sf.STATE_FIELDS + ("status", "n_sub")})
+        res["fp64"] = dict(ms=ms_d, wall=wall_d, stats=st_d, steps=k64, launch=sd.get_launch())
+        sd.close()
+    # ---- end to end through the public API with host buffers
+    host_in = {k: torch.as_tensor(cells[k]).pin_memory() for k in sf.STATE_FIELDS + sf.INPUT_FIELDS}
+    host_out = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in sf.STATE_FIELDS}
+    host_out["status"] = torch.empty(n, dtype=torch.uint8).pin_memory()
+    e2e_times = []
+    h2d = sum(v.numel() * v.element_size() for v in host_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+    for i in range(args.warmup + args.steps):
+        barrier(world)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k, v in host_in.items():
+            d[k].copy_(v, non_blocking=True)
+        sm.step_batched(d, off, bdt, cd)
+        for k, v in host_out.items():
+            v.copy_(d[k], non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(a.elapsed_time(b))
+    e2e_ms = float(np.mean(e2e_times))
+    sm.close()
+
+    # cross-rank aggregation: max time over ranks
+    ms_m_max = allreduce_max(ms_m, world)
+    e2e_max = allreduce_max(e2e_ms, world)
+    total_cells = n * world
+    value = total_cells / (ms_m_max * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_m_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+        "config": dict(desc, precision="mixed", path="sfchem_step_batched (persistent kernel, CUDA graph)",
+                       l2="inputs (2.4 GB) larger than L2; state reset from a device copy before each step",
+                       parallelism=f"independent cell shards x{world}"),
+        "e2e": {"value": total_cells / (e2e_max * 1e-3), "unit": "cell-updates/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,   # per step: schedule kernel + persistent solver kernel
+        "clocks": clk,
+    }
+    if "fp64" in res:
+        ms_d_max = allreduce_max(res["fp64"]["ms"], world)
+        line["fp64"] = {"value": total_cells / (ms_d_max * 1e-3), "ms_per_step": ms_d_max,
+                        "steps": res["fp64"]["steps"], "launch": res["fp64"]["launch"]}
+        line["speedup_mixed_vs_fp64"] = ms_d_max / ms_m_max
+    st = res["mixed"]["stats"]
+    line["substeps_per_cell"] = st["substeps"] / max(st["cells"], 1)
+    line["tight_fraction"] = st["tight_cells"] / max(st["cells"], 1)
+    line["launch"] = res["mixed"]["launch"]
+    # roofline of the dominant kernel (the mixed solver kernel)
+    line["roofline"] = roofline(res, clk, n)
+    if rank == 0 and not args.no_cpu:
+        line["error_vs_oracle"] = error_vs_oracle(cells, off, bdt, cd, out_m, out_d, args.sample)
+        line["cpu_baseline"] = cpu_baseline(cells, off, bdt, cd, args.cpu_seconds)
+    return line
+
+
+def roofline(res, clk, n_cells):
+    """ALU roofline of the mixed solver kernel.  Algorithmic work per
+    cell-substep (WORK_PER_SUBSTEP) x substeps of one launch / kernel time;
+    the peak is the FP pipe the kernel is bound by, from unit counts and the
+    maximum SM clock."""
+    st = res["mixed"]["stats"]
+    subs = st["substeps"] / max(st["calls"], 1)
+    ms = res["mixed"]["ms"]
+    w = WORK_PER_SUBSTEP["mixed"]
+    f_mhz = (clk.get("sm_max_mhz") or 2070.0)
+    peak64 = N_SM * FP64_FLOP_PER_SM_CLK * f_mhz * 1e6 / 1e12
+    peak32 = N_SM * FP32_FLOP_PER_SM_CLK * f_mhz * 1e6 / 1e12
+    out = {"bound": "alu", "unit": "TFLOP/s", "traffic": None,
+           "substeps_per_launch": subs, "kernel_ms": ms}
+    if w["fp64_flops"] is None:
+        out.update(achieved=None, peak=peak64, frac=None, pipe="fp64",
+                   note="per-substep work not yet counted")
+        return out
+    a64 = w["fp64_flops"] * subs / (ms * 1e-3) / 1e12
+    a32 = w["fp32_flops"] * subs / (ms * 1e-3) / 1e12
+    f64, f32 = a64 / peak64, a32 / peak32
+    if f64 >= f32:
+        out.update(achieved=a64, peak=peak64, frac=f64, pipe="fp64", other={"fp32_frac": f32})
+    else:
+        out.update(achieved=a32, peak=peak32, frac=f32, pipe="fp32", other={"fp64_frac": f64})
+    return out
+
+
+def error_vs_oracle(cells, off, bdt, cd, out_m, out_d, sample):
+    """Mixed and FP64 results against the oracle on a seeded sample of cells."""
+    import oracle
+    n = len(cells["n_H"])
+    idx = np.sort(np.random.default_rng(123).choice(n, min(sample, n), replace=False))
+    blk = np.searchsorted(off, idx, side="right") - 1
+    sub = inputs.subset(cells, idx)
+    ref = oracle.li_step(sub, bdt[blk], cd)
+    out = {"sample_cells": int(idx.size)}
+    for name, got in (("mixed", out_m), ("fp64", out_d)):
+        if got is None:
+            continue
+        res = {}
+        for k in ("T_g", "T_d", "E_IR", "y_H2", "y_e"):
+            a, b = got[k][idx], ref[k]
+            floor = 1e-6 if k.startswith("y_") else 1e-300
+            e = np.abs(a - b) / np.maximum(np.abs(b), floor)
+            res[k] = {"max": float(e.max()), "p99": float(np.percentile(e, 99)), "median": float(np.median(e))}
+        res["n_sub_mismatch"] = int((got["n_sub"][idx] != ref["n_sub"]).sum())
+        out[name] = res
+    out["metric"] = "relative error; abundances below 1e-6 in units of 1e-6"
+    return out
+
+
+def cpu_baseline(cells, off, bdt, cd, target_s):
+    """The oracle on the host cores, on a bounded sample of the workload."""
+    import oracle
+    n = len(cells["n_H"])
+    rng = np.random.default_rng(7)
+    m = 1024
+    while True:
+        idx = np.sort(rng.choice(n, min(m, n), replace=False))
+        blk = np.searchsorted(off, idx, side="right") - 1
+        sub = inputs.subset(cells, idx)
+        t0 = time.perf_counter()
+        oracle.li_step(sub, bdt[blk], cd)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * target_s or m >= n or m >= (1 << 22):
+            break
+        m = int(min(n, max(2 * m, m * 0.6 * target_s / max(dt, 1e-3))))
+    cores = os.cpu_count()
+    return {"value": idx.size / dt, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{idx.size} seeded cells of the workload, one step, {dt:.1f} s wall on {cores} threads"}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    """The oracle (plain FP64 CPU LI step) timed on the host cores, each step
+    one bounded sample of the same workload."""
+    import oracle
+    cells, off, bdt, cd, desc = make_workload(args.workload, 0)
+    n = len(cells["n_H"])
+    rng = np.random.default_rng(99)
+    # size the per-step sample so the whole run stays within a few minutes
+    probe = np.sort(rng.choice(n, min(2048, n), replace=False))
+    t0 = time.perf_counter()
+    oracle.li_step(inputs.subset(cells, probe), bdt[np.searchsorted(off, probe, side="right") - 1], cd)
+    per_cell = (time.perf_counter() - t0) / probe.size
+    budget = 120.0 / max(args.steps + args.warmup, 1)
+    m = int(min(n, max(1024, budget / max(per_cell, 1e-9))))
+    times = []
+    for i in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(n, m, replace=False))
+        sub = inputs.subset(cells, idx)
+        blk = np.searchsorted(off, idx, side="right") - 1
+        t0 = time.perf_counter()
+        oracle.li_step(sub, bdt[blk], cd)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    sec = float(np.mean(times))
+    value = m / sec
+    cores = os.cpu_count()
+    return {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": dict(desc, precision="fp64", path="CPU oracle (OpenMP over cells)",
+                           sample_cells_per_step=m),
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{m} seeded cells of the workload per step"},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------- plumbing
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+_PG = {"on": False}
+
+
+def init_dist(world, local_rank):
+    if world > 1 and not _PG["on"]:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend)
+        _PG["on"] = True
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x: float, world: int) -> float:
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    init_dist(world, local)
+    line = run_ours(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

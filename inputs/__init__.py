@@ -232,3 +232,16 @@ def subset(cells: dict, idx) -> dict:
 
 def concat(*parts: dict) -> dict:
     return {k: np.concatenate([p[k] for p in parts]) for k in FIELDS}
+
+
+def block_major(cells: dict, n: int, b: int = 16):
+    """Reorder an n^3 x-fastest grid into contiguous b^3 blocks (the layout of
+    a block-structured AMR code).  Returns (cells, block_offset)."""
+    assert n % b == 0
+    nb = n // b
+    out = {}
+    for k, v in cells.items():
+        a = np.asarray(v).reshape(nb, b, nb, b, nb, b)          # (z, z', y, y', x, x')
+        out[k] = np.ascontiguousarray(a.transpose(0, 2, 4, 1, 3, 5)).reshape(-1)
+    block_offset = np.arange(nb ** 3 + 1, dtype=np.int64) * b ** 3
+    return out, block_offset

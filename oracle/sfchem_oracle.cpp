@@ -11,7 +11,9 @@
 // no finite differences); the dust / IR / gas-grain rows are written with the
 // coefficients printed in Appendix C (Eqs. ap_eq:Td2, the IR row and
 // ap_eq:Tg_2 with beta_d, beta_IR, gamma_d, zeta).  A 5x5 system is solved by
-// textbook Gaussian elimination with partial pivoting.
+// textbook Gaussian elimination with partial pivoting after an exact
+// power-of-two equilibration of its rows and columns, refined twice with
+// residuals computed to twice the working precision.
 //
 // Readings of passages the paper leaves open are marked "reading:"; the
 // stand-ins for physics the paper only cites ("see the reference") are marked
@@ -371,12 +373,33 @@ void assemble(const System &s, double dt, const oracle_config &c, double A[25], 
     }
 }
 
-// Gaussian elimination, partial pivoting (largest |a| in the column, lowest
-// row index on ties), back substitution.
-int solve_n(int N, const double *Ain, const double *bin, double *x) {
-  double A[25], b[5];
+// Gaussian elimination with partial pivoting (largest |a| in the column,
+// lowest row index on ties) and back substitution, on a system that has
+// been equilibrated by powers of two (exact, no rounding): every column,
+// then every row, is scaled so that its largest entry lies in [0.5, 1).
+int ge_solve(int N, const double *Ain, const double *bin, double *x) {
+  double A[25], b[5], cs[5];
   std::memcpy(A, Ain, sizeof(double) * N * N);
   std::memcpy(b, bin, sizeof(double) * N);
+  for (int j = 0; j < N; ++j) {
+    double m = 0.0;
+    for (int i = 0; i < N; ++i) m = std::max(m, std::fabs(A[i * N + j]));
+    if (m == 0.0) return -1;
+    int e;
+    std::frexp(m, &e);
+    cs[j] = std::ldexp(1.0, -e);
+    for (int i = 0; i < N; ++i) A[i * N + j] *= cs[j];
+  }
+  for (int i = 0; i < N; ++i) {
+    double m = 0.0;
+    for (int j = 0; j < N; ++j) m = std::max(m, std::fabs(A[i * N + j]));
+    if (m == 0.0) return -1;
+    int e;
+    std::frexp(m, &e);
+    double rs = std::ldexp(1.0, -e);
+    for (int j = 0; j < N; ++j) A[i * N + j] *= rs;
+    b[i] *= rs;
+  }
   for (int col = 0; col < N; ++col) {
     int p = col;
     for (int r = col + 1; r < N; ++r)
@@ -396,6 +419,43 @@ int solve_n(int N, const double *Ain, const double *bin, double *x) {
     double s = b[r];
     for (int j = r + 1; j < N; ++j) s -= A[r * N + j] * x[j];
     x[r] = s / A[r * N + r];
+  }
+  for (int j = 0; j < N; ++j) x[j] *= cs[j];
+  return 0;
+}
+
+// r = b - A x with the products and sums carried exactly to twice the
+// working precision (error-free transformations: TwoProduct through fma,
+// TwoSum), rounded once at the end.
+void residual_dd(int N, const double *A, const double *b, const double *x, double *r) {
+  for (int i = 0; i < N; ++i) {
+    double s = b[i], c = 0.0;
+    for (int j = 0; j < N; ++j) {
+      double p = -A[i * N + j] * x[j];
+      double pe = std::fma(-A[i * N + j], x[j], -p);   // exact error of the product
+      double t = s + p;
+      double z = t - s;
+      double se = (s - (t - z)) + (p - z);             // exact error of the sum
+      s = t;
+      c += pe + se;
+    }
+    r[i] = s + c;
+  }
+}
+
+// Exact (to rounding) solution of A x = b for N <= 5.  The rows and columns
+// carry different units (abundances, kelvin, erg cm^-3) that span ~30
+// decades, and small components of x (the electron update next to a large
+// temperature update) must come out with full relative accuracy, so the
+// equilibrated elimination is followed by two steps of iterative refinement
+// with residuals computed to twice the working precision.
+int solve_n(int N, const double *A, const double *b, double *x) {
+  if (ge_solve(N, A, b, x) != 0) return -1;
+  for (int it = 0; it < 2; ++it) {
+    double r[5], d[5];
+    residual_dd(N, A, b, x, r);
+    if (ge_solve(N, A, r, d) != 0) return -1;
+    for (int j = 0; j < N; ++j) x[j] += d[j];
   }
   return 0;
 }
@@ -430,7 +490,9 @@ int newton_dust(double u[5], const double u0[5], double dt, const CellIn &ci, co
                 double tol, int limit) {
   bool frTd = bit(c.flags, ORACLE_F_FREEZE_TD), frE = bit(c.flags, ORACLE_F_FREEZE_EIR);
   if (frTd && frE) return 0;
-  for (int it = 1; it <= limit; ++it) {
+  bool polish = false;
+  for (int it = 1; it <= limit + 1; ++it) {
+    if (it > limit && !polish) break;
     DustTerms d = dust_terms(u[2], u[3], u[4], ci, c);
     double acTd3 = a_rad * c_light * std::pow(u[3], 3);
     double G4 = ci.Cd * (u[3] - u0[3]) - dt * d.D;
@@ -442,11 +504,15 @@ int newton_dust(double u[5], const double u0[5], double dt, const CellIn &ci, co
     if (frE) { J[2] = 0.0; J[3] = 1.0; rhs[1] = 0.0; }
     double del[2];
     if (solve_n(2, J, rhs, del) != 0) return -it;
-    double lam = damp_factor(u[3], u[4], del[0], del[1]);
+    double lam = polish ? 1.0 : damp_factor(u[3], u[4], del[0], del[1]);
     u[3] += lam * del[0];
     u[4] += lam * del[1];
     project(u);
-    if (lam == 1.0 && std::fabs(del[0]) <= tol * u[3] && std::fabs(del[1]) <= tol * u[4]) return it;
+    // reading: once the stopping test holds, one more full Newton step
+    // polishes the iterate (not counted), so that the result does not depend
+    // on which iteration the tolerance test happened to pass
+    if (polish) return it - 1;
+    if (lam == 1.0 && std::fabs(del[0]) <= tol * u[3] && std::fabs(del[1]) <= tol * u[4]) polish = true;
   }
   return -limit;
 }

@@ -132,7 +132,9 @@ void oracle_rhs(double n_H, const double u[5], double G0, double n_EUV,
                 double N_H2, double cd_factor, const oracle_config *cfg,
                 double dudt[5]);
 
-/* Gaussian elimination with partial pivoting on a row-major 5x5. */
+/* Solve a row-major 5x5 system: power-of-two row/column equilibration,
+ * Gaussian elimination with partial pivoting, two refinement steps with
+ * double-word residuals.  Returns -1 when singular. */
 int oracle_solve5(const double A[25], const double b[5], double x[5]);
 
 #ifdef __cplusplus

@@ -1,0 +1,11 @@
+// launch.h -- host-side entry points of the kernels (internal to libsfchem).
+#pragma once
+#include <cuda_runtime.h>
+#include "li_kernels.cuh"
+
+namespace sfc {
+cudaError_t launch_li_fp64(const KArgs &a, int grid, int tpb, cudaStream_t s);
+cudaError_t launch_li_mixed(const KArgs &a, int grid, int tpb, cudaStream_t s);
+cudaError_t occupancy_li_fp64(int tpb, int *ctas_per_sm);
+cudaError_t occupancy_li_mixed(int tpb, int *ctas_per_sm);
+}  // namespace sfc

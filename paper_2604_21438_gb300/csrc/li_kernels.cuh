@@ -1,0 +1,437 @@
+// li_kernels.cuh -- per-cell substep driver, 5x5 LU, tight-coupling Newton
+// iteration and the persistent lane-refill kernel of libsfchem.
+//
+// Execution model: one thread per cell.  A persistent grid of warps pulls
+// chunks of cells from a global counter (one atomic per chunk).  Inside a
+// warp every lane owns one cell and advances it one LI substep per loop
+// trip; a lane whose cell has reached dt_hydro stores it and is refilled from
+// the warp's chunk before the next trip (warp-vote refill), so lanes with
+// long substep sequences do not hold idle lanes hostage.  There are no waits
+// on other threads anywhere, so the kernel always terminates: every cell
+// loop is bounded by n_sub_max, every Newton loop by nr_itr_limit.
+#pragma once
+#include "li_device.cuh"
+
+namespace sfc {
+
+// ------------------------------------------------------------------- 5x5 LU
+// Gaussian elimination with partial pivoting (largest |a| in the column, the
+// first such row on ties).  Row exchanges touch only the active columns, and
+// the multipliers stay where they were computed, so a second right-hand side
+// can be solved by replaying the same exchanges (sw) and eliminations.
+template <typename W> struct LU5 {
+  W a[5][5];
+  W inv[5];
+  bool sw[10];
+};
+
+template <typename W>
+__device__ __forceinline__ bool lu5_factor(LU5<W> &L) {
+  int s = 0;
+#pragma unroll
+  for (int col = 0; col < 5; ++col) {
+#pragma unroll
+    for (int r = col + 1; r < 5; ++r) {
+      const bool ex = M<W>::abs(L.a[r][col]) > M<W>::abs(L.a[col][col]);
+      L.sw[s++] = ex;
+#pragma unroll
+      for (int j = col; j < 5; ++j) {
+        const W x = L.a[col][j], y = L.a[r][j];
+        L.a[col][j] = ex ? y : x;
+        L.a[r][j] = ex ? x : y;
+      }
+    }
+    const W piv = L.a[col][col];
+    if (!(M<W>::abs(piv) > W(0))) return false;
+    const W ip = W(1) / piv;
+    L.inv[col] = ip;
+#pragma unroll
+    for (int r = col + 1; r < 5; ++r) {
+      const W f = L.a[r][col] * ip;
+      L.a[r][col] = f;
+#pragma unroll
+      for (int j = col + 1; j < 5; ++j) L.a[r][j] -= f * L.a[col][j];
+    }
+  }
+  return true;
+}
+
+template <typename W, typename V>
+__device__ __forceinline__ void lu5_solve(const LU5<W> &L, V b[5]) {
+  int s = 0;
+#pragma unroll
+  for (int col = 0; col < 5; ++col) {
+#pragma unroll
+    for (int r = col + 1; r < 5; ++r) {
+      const bool ex = L.sw[s++];
+      const V x = b[col], y = b[r];
+      b[col] = ex ? y : x;
+      b[r] = ex ? x : y;
+    }
+#pragma unroll
+    for (int r = col + 1; r < 5; ++r) b[r] -= V(L.a[r][col]) * b[col];
+  }
+#pragma unroll
+  for (int r = 4; r >= 0; --r) {
+    V acc = b[r];
+#pragma unroll
+    for (int j = r + 1; j < 5; ++j) acc -= V(L.a[r][j]) * b[j];
+    b[r] = acc * V(L.inv[r]);
+  }
+}
+
+// ----------------------------------------------------------- projection
+// Positivity and conservation after an update: 0 <= y_e <= 1,
+// 0 <= y_H2 <= (1 - y_e)/2 (so y_H = 1 - 2 y_H2 - y_e >= 0), temperatures at
+// least T_CMB, E_IR at least the CMB-equivalent energy density.  FP64.
+__device__ __forceinline__ void project(double u[5]) {
+  u[1] = fmin(fmax(u[1], 0.0), 1.0);
+  u[0] = fmin(fmax(u[0], 0.0), (1.0 - u[1]) * 0.5);
+  u[2] = fmax(u[2], TCMB);
+  u[3] = fmax(u[3], TCMB);
+  u[4] = fmax(u[4], EFLOOR);
+}
+
+// A Newton correction of the tight-coupling iteration is scaled by one
+// factor so that T_d changes by at most 2x and E_IR by at most 16x.
+__device__ __forceinline__ double damp_factor(double Td, double E, double dTd, double dE) {
+  double lam = 1.0;
+  if (Td + dTd > 2.0 * Td) lam = fmin(lam, Td / dTd);
+  if (Td + dTd < 0.5 * Td) lam = fmin(lam, -0.5 * Td / dTd);
+  if (E + dE > 16.0 * E) lam = fmin(lam, 15.0 * E / dE);
+  if (E + dE < E / 16.0) lam = fmin(lam, -(15.0 / 16.0) * E / dE);
+  return lam;
+}
+
+// Tight coupling (Sec. 2.2.8): Newton iteration of the backward-Euler
+// residual of the dust row (Eq. ap_eq:dust_temp) and the IR row
+// (Eq. ap_eq:Eir) at the substep's new T_g and abundances.  Returns the
+// iteration count, negative when nr_itr_limit was reached.
+template <typename W>
+__device__ __forceinline__ int newton_dust(double u[5], const double u0[5], double dt, const CellK &c,
+                                           const DevCfg &cfg) {
+  typedef M<W> m;
+  const bool frTd = cfg.flags & F_FTD, frE = cfg.flags & F_FE;
+  if (frTd && frE) return 0;
+  const uint32_t pm = cfg.pmask;
+  const W T = W(u[2]);
+  const W G = W(c.Gpre) * m::sqrt(T);
+  const W gam = W(1) - W(0.8) * m::exp(W(-TLOW) / T);
+  const W Cd = W(c.Cd), rho = W(c.rho), fd = W(c.fd), dtw = W(dt);
+  bool polish = false;
+  for (int it = 1; it <= cfg.nr_itr_limit + 1; ++it) {
+    if (it > cfg.nr_itr_limit && !polish) break;
+    const W Td = W(u[3]), E = W(u[4]);
+    W be_d, ba_d, be_i, ba_i;
+    const W kd = kappa_w<W>(Td, be_d, ba_d);
+    const W TIR = m::sqrt(m::sqrt(W(1e-4 / ARAD) * E));
+    const W ki = kappa_w<W>(TIR, be_i, ba_i);
+    const W acTd3 = W(ARAD * CLIGHT) * Td * Td * Td;
+    const W emit = (pm & P_EMIT) ? kd * acTd3 * Td : W(0);
+    const W irabs = (pm & P_IRABS) ? ki * W(CRED) * E : W(0);
+    const W beta_d = (pm & P_EMIT) ? be_d : W(0);
+    const W beta_IR = (pm & P_IRABS) ? ba_i : W(0);
+    const W D = irabs + W(c.EUV) - emit - G * gam * W(u[3] - u[2]);
+    const W I = rho * fd * (emit - irabs);
+    // relative unknowns (dT_d/T_d, dE/E); rows scaled by C_d T_d and E
+    W r0 = W(-(u[3] - u0[3]) / u[3]) + dtw * D / (Cd * Td);
+    W r1 = W(-(u[4] - u0[4]) / u[4]) + dtw * I / E;
+    W J00 = W(1) + dtw * (G * gam + acTd3 * beta_d) / Cd;
+    W J01 = -dtw * W(CRED) * beta_IR * E / (Cd * Td);
+    W J10 = -dtw * rho * fd * acTd3 * beta_d * Td / E;
+    W J11 = W(1) + dtw * rho * W(CRED) * fd * beta_IR;
+    if (frTd) { J00 = W(1); J01 = W(0); r0 = W(0); }
+    if (frE) { J10 = W(0); J11 = W(1); r1 = W(0); }
+    const W det = J00 * J11 - J01 * J10;
+    if (!(m::abs(det) > W(0))) return -it;
+    const W x0 = (r0 * J11 - J01 * r1) / det;
+    const W x1 = (J00 * r1 - J10 * r0) / det;
+    const double d0 = double(x0) * u[3], d1 = double(x1) * u[4];
+    const double lam = polish ? 1.0 : damp_factor(u[3], u[4], d0, d1);
+    u[3] += lam * d0;
+    u[4] += lam * d1;
+    project(u);
+    // after the stopping test holds, one more full step (not counted) makes
+    // the result independent of where the test happened to pass
+    if (polish) return it - 1;
+    if (lam == 1.0 && fabs(d0) <= cfg.nr_tol * u[3] && fabs(d1) <= cfg.nr_tol * u[4]) polish = true;
+  }
+  return -cfg.nr_itr_limit;
+}
+
+// ------------------------------------------------------------- one cell
+struct CellRun {
+  double u[5];   // y_H2, y_e, T_g, T_d, E_IR
+  double t;      // time advanced so far in this call
+  CellK k;
+  int32_t nsub, nitr;
+  uint8_t st;
+  int8_t mode;   // -1 undecided, 0 subcycling, 1 tight coupling
+};
+
+__device__ __forceinline__ bool valid_input(double n, double Tg, double Td, double E, double y2,
+                                            double ye, double G0, double nE, double NH2, double dt) {
+  const double v[10] = {n, Tg, Td, E, y2, ye, G0, nE, NH2, dt};
+#pragma unroll
+  for (int i = 0; i < 10; ++i)
+    if (!isfinite(v[i])) return false;
+  if (!(n > 0.0 && Tg > 0.0 && Td > 0.0 && E >= 0.0 && y2 >= 0.0 && ye >= 0.0 && ye <= 1.0)) return false;
+  if (!(2.0 * y2 + ye <= 1.0 + 1e-9)) return false;
+  if (!(G0 >= 0.0 && nE >= 0.0 && NH2 >= 0.0 && dt >= 0.0)) return false;
+  return true;
+}
+
+// One LI substep of Sec. 2.2.8; returns true when the cell is finished.
+// MIXED: W = float for rates, Jacobian and LU, with one FP64 residual
+// refinement of the scaled 5x5 solve.
+template <typename W, bool MIXED>
+__device__ __forceinline__ bool li_substep(CellRun &c, const DevCfg &cfg) {
+  Sys<W> S;
+  eval_system<W>(c.u, c.k, cfg, S);
+  const double dt_h = c.k.dt_h;
+  if (c.mode < 0) {
+    // estimated subcycles dt_hydro / (f_chem dt_dust) against N_cyc, from the start state
+    const bool tight = !(dt_h * double(S.rate_dust) < double(cfg.n_cyc) * cfg.f_chem);
+    c.mode = tight ? 1 : 0;
+    if (tight) c.st |= ST_TIGHT;
+  }
+  double inv = fmax(double(S.rate_chem), double(S.rate_energy));
+  if (c.mode == 0) inv = fmax(inv, double(S.rate_dust));
+  const double dtc = inv > 0.0 ? cfg.f_chem / inv : __longlong_as_double(0x7ff0000000000000LL);
+  const double rem = dt_h - c.t;
+  const bool last = (dtc >= rem) || (rem - dtc <= 1e-12 * dt_h);
+  const double dts = last ? rem : dtc;
+  if (!(dts > 0.0) || !isfinite(dts)) { c.st |= ST_BADSTEP; return true; }
+  // A = I - dt J, b = dt F (scaled rows and columns)
+  LU5<W> L;
+  W x[5];
+  const W dw = W(dts);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) L.a[i][j] = (i == j ? W(1) : W(0)) - dw * S.J[i][j];
+    x[i] = dw * S.F[i];
+  }
+  if (!lu5_factor<W>(L)) { c.st |= ST_BADSTEP; return true; }
+  lu5_solve<W, W>(L, x);
+  double xd[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) xd[i] = double(x[i]);
+  if (MIXED) {
+    // one FP64 residual-refinement pass: r = dt F - (I - dt J) x, over the
+    // structural non-zeros of J (rows 0-2: columns 0-3; row 3: 2-4; row 4: 3-4)
+    double r[5];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s = fma(double(S.J[i][j]), xd[j], s);
+      r[i] = fma(dts, double(S.F[i]) + s, -xd[i]);
+    }
+    {
+      double s = fma(double(S.J[3][2]), xd[2], fma(double(S.J[3][3]), xd[3], double(S.J[3][4]) * xd[4]));
+      r[3] = fma(dts, double(S.F[3]) + s, -xd[3]);
+      s = fma(double(S.J[4][3]), xd[3], double(S.J[4][4]) * xd[4]);
+      r[4] = fma(dts, double(S.F[4]) + s, -xd[4]);
+    }
+    W rw[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) rw[i] = W(r[i]);
+    lu5_solve<W, W>(L, rw);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) xd[i] += double(rw[i]);
+  }
+  double u0[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) u0[i] = c.u[i];
+  c.u[0] += xd[0];
+  c.u[1] += xd[1];
+  c.u[2] = fma(c.u[2], xd[2], c.u[2]);
+  c.u[3] = fma(c.u[3], xd[3], c.u[3]);
+  c.u[4] = fma(c.u[4], xd[4], c.u[4]);
+  project(c.u);
+  if (c.mode == 1) {
+    // the iteration starts from the LI update of (T_d, E_IR), limited like a Newton correction
+    const double lam = damp_factor(u0[3], u0[4], c.u[3] - u0[3], c.u[4] - u0[4]);
+    if (lam < 1.0) {
+      c.u[3] = u0[3] + lam * (c.u[3] - u0[3]);
+      c.u[4] = u0[4] + lam * (c.u[4] - u0[4]);
+      project(c.u);
+    }
+    int it = newton_dust<W>(c.u, u0, dts, c.k, cfg);
+    if (it < 0) { c.st |= ST_NOCONV; it = -it; }
+    c.nitr += it;
+  }
+  c.t = last ? dt_h : c.t + dts;
+  c.nsub++;
+  if (last) return true;
+  if (c.nsub >= cfg.n_sub_max) { c.st |= ST_CAP; return true; }
+  return false;
+}
+
+// H- abundance from the equilibrium of reactions H2 and H3 (unmasked rates)
+__device__ __forceinline__ double y_hminus(double T, double ye) {
+  const double lnT = log(T);
+  const double k2 = exp(-41.11005943727161 + 0.928 * lnT - T * (1.0 / 16200.0));
+  const double N = exp(0.098493 * lnT) + 0.32852 * exp(0.5561 * lnT) + 2.771e-7 * exp(2.1826 * lnT);
+  const double D = 1.0 + 6.191e-3 * exp(1.0461 * lnT) + 8.9712e-11 * exp(3.0424 * lnT) +
+                   3.2576e-14 * exp(3.7741 * lnT);
+  const double k3 = 1.35e-9 * N / D;
+  return k2 * ye / k3;
+}
+
+// ------------------------------------------------------------ the kernel
+struct DevStats {
+  unsigned long long cells, substeps, newton, tight, cap, noconv, bad, badstep;
+  unsigned int max_sub, pad;
+};
+
+struct KArgs {
+  // state (device pointers)
+  const double *nH;
+  double *Tg, *Td, *E, *y2, *ye, *yH, *yHp, *yHm;
+  uint8_t *status;
+  int32_t *nsub;
+  const double *G0, *nEUV, *NH2;
+  // work: flat (ch_start == nullptr) or a chunk table
+  int64_t n_cells;
+  double dt;
+  int32_t chunk;
+  int32_t n_chunks;
+  const int64_t *ch_start;
+  const int32_t *ch_count;
+  const int32_t *ch_block;
+  const double *block_dt;
+  float *block_cost;
+  double cd_factor;
+  unsigned long long *counter;
+  DevStats *stats;
+  DevCfg cfg;
+};
+
+template <typename W, bool MIXED>
+__device__ __forceinline__ void li_persistent_body(const KArgs &a) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const DevCfg cfg = a.cfg;
+  // warp-uniform chunk cursor
+  int64_t cpos = 0, cend = 0;
+  int32_t cblock = -1;
+  double cdt = a.dt;
+  bool exhausted = false;
+  // lane state
+  bool have = false;
+  CellRun c;
+  int64_t idx = 0;
+  int32_t blk = -1;
+  // lane statistics
+  unsigned long long s_cells = 0, s_sub = 0, s_newton = 0, s_tight = 0, s_cap = 0, s_noconv = 0,
+                     s_bad = 0, s_badstep = 0;
+  unsigned int s_max = 0;
+
+  while (true) {
+    unsigned need = __ballot_sync(FULL, !have);
+    while (need != 0u && !exhausted) {
+      if (cpos >= cend) {
+        unsigned long long ci = 0;
+        if (lane == 0) ci = atomicAdd(a.counter, 1ull);
+        ci = __shfl_sync(FULL, ci, 0);
+        if (ci >= (unsigned long long)a.n_chunks) { exhausted = true; break; }
+        if (a.ch_start) {
+          cpos = a.ch_start[ci];
+          cend = cpos + a.ch_count[ci];
+          cblock = a.ch_block[ci];
+          cdt = a.block_dt[cblock];
+        } else {
+          cpos = (int64_t)ci * a.chunk;
+          cend = min(cpos + (int64_t)a.chunk, a.n_cells);
+        }
+        continue;
+      }
+      const int avail = (int)(cend - cpos);
+      const int k = __popc(need);
+      const int take = min(k, avail);
+      const int rank = __popc(need & lt_mask);
+      if (((need >> lane) & 1u) && rank < take) {
+        idx = cpos + rank;
+        blk = cblock;
+        const double n = __ldg(a.nH + idx), G0 = __ldg(a.G0 + idx), nE = __ldg(a.nEUV + idx),
+                     NH2 = __ldg(a.NH2 + idx);
+        c.u[0] = a.y2[idx]; c.u[1] = a.ye[idx]; c.u[2] = a.Tg[idx]; c.u[3] = a.Td[idx]; c.u[4] = a.E[idx];
+        c.t = 0.0; c.nsub = 0; c.nitr = 0; c.st = 0; c.mode = -1;
+        s_cells++;
+        if (!valid_input(n, c.u[2], c.u[3], c.u[4], c.u[0], c.u[1], G0, nE, NH2, cdt)) {
+          c.st = ST_BAD;
+          s_bad++;
+          if (a.yH) a.yH[idx] = __longlong_as_double(0x7ff8000000000000LL);
+          if (a.yHp) a.yHp[idx] = __longlong_as_double(0x7ff8000000000000LL);
+          if (a.yHm) a.yHm[idx] = __longlong_as_double(0x7ff8000000000000LL);
+          if (a.status) a.status[idx] = ST_BAD;
+          if (a.nsub) a.nsub[idx] = 0;
+        } else {
+          make_cellk(c.k, n, G0, nE, NH2, a.cd_factor, cdt, cfg);
+          project(c.u);
+          have = true;
+          if (cdt == 0.0) have = false;   // nothing to integrate: store the projected state
+          if (!have) {
+            a.y2[idx] = c.u[0]; a.ye[idx] = c.u[1]; a.Tg[idx] = c.u[2]; a.Td[idx] = c.u[3]; a.E[idx] = c.u[4];
+            if (a.yH) a.yH[idx] = 1.0 - 2.0 * c.u[0] - c.u[1];
+            if (a.yHp) a.yHp[idx] = c.u[1];
+            if (a.yHm) a.yHm[idx] = y_hminus(c.u[2], c.u[1]);
+            if (a.status) a.status[idx] = 0;
+            if (a.nsub) a.nsub[idx] = 0;
+          }
+        }
+      }
+      cpos += take;
+      need = __ballot_sync(FULL, !have);
+    }
+    if (!__any_sync(FULL, have)) break;
+    if (have) {
+      if (li_substep<W, MIXED>(c, cfg)) {
+        a.y2[idx] = c.u[0]; a.ye[idx] = c.u[1]; a.Tg[idx] = c.u[2]; a.Td[idx] = c.u[3]; a.E[idx] = c.u[4];
+        if (a.yH) a.yH[idx] = 1.0 - 2.0 * c.u[0] - c.u[1];
+        if (a.yHp) a.yHp[idx] = c.u[1];
+        if (a.yHm) a.yHm[idx] = y_hminus(c.u[2], c.u[1]);
+        if (a.status) a.status[idx] = c.st;
+        if (a.nsub) a.nsub[idx] = c.nsub;
+        s_sub += (unsigned long long)c.nsub;
+        s_newton += (unsigned long long)c.nitr;
+        s_max = max(s_max, (unsigned int)c.nsub);
+        if (c.st & ST_TIGHT) s_tight++;
+        if (c.st & ST_CAP) s_cap++;
+        if (c.st & ST_NOCONV) s_noconv++;
+        if (c.st & ST_BADSTEP) s_badstep++;
+        if (a.block_cost && blk >= 0) atomicAdd(a.block_cost + blk, (float)c.nsub);
+        have = false;
+      }
+    }
+  }
+  // statistics: warp reduction, one set of atomics per warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s_cells += __shfl_down_sync(FULL, s_cells, o);
+    s_sub += __shfl_down_sync(FULL, s_sub, o);
+    s_newton += __shfl_down_sync(FULL, s_newton, o);
+    s_tight += __shfl_down_sync(FULL, s_tight, o);
+    s_cap += __shfl_down_sync(FULL, s_cap, o);
+    s_noconv += __shfl_down_sync(FULL, s_noconv, o);
+    s_bad += __shfl_down_sync(FULL, s_bad, o);
+    s_badstep += __shfl_down_sync(FULL, s_badstep, o);
+    s_max = max(s_max, __shfl_down_sync(FULL, s_max, o));
+  }
+  if (lane == 0 && s_cells) {
+    atomicAdd(&a.stats->cells, s_cells);
+    atomicAdd(&a.stats->substeps, s_sub);
+    if (s_newton) atomicAdd(&a.stats->newton, s_newton);
+    if (s_tight) atomicAdd(&a.stats->tight, s_tight);
+    if (s_cap) atomicAdd(&a.stats->cap, s_cap);
+    if (s_noconv) atomicAdd(&a.stats->noconv, s_noconv);
+    if (s_bad) atomicAdd(&a.stats->bad, s_bad);
+    if (s_badstep) atomicAdd(&a.stats->badstep, s_badstep);
+    atomicMax(&a.stats->max_sub, s_max);
+  }
+}
+
+}  // namespace sfc

@@ -1,0 +1,28 @@
+// li_mixed.cu -- the mixed-precision LI kernel: rate coefficients, heating
+// and cooling, Jacobian assembly and the 5x5 LU in FP32; the state, the time
+// accounting, one residual-refinement pass of the solve, the update and the
+// conservation projection in FP64.
+#include "li_kernels.cuh"
+#include "launch.h"
+
+namespace sfc {
+
+template <int TPB>
+__global__ void __launch_bounds__(TPB) sfchem_li_mixed(KArgs a) {
+  li_persistent_body<float, true>(a);
+}
+
+cudaError_t launch_li_mixed(const KArgs &a, int grid, int tpb, cudaStream_t s) {
+  if (tpb == 256) sfchem_li_mixed<256><<<grid, 256, 0, s>>>(a);
+  else if (tpb == 64) sfchem_li_mixed<64><<<grid, 64, 0, s>>>(a);
+  else sfchem_li_mixed<128><<<grid, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t occupancy_li_mixed(int tpb, int *ctas_per_sm) {
+  if (tpb == 256) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, sfchem_li_mixed<256>, 256, 0);
+  if (tpb == 64) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, sfchem_li_mixed<64>, 64, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, sfchem_li_mixed<128>, 128, 0);
+}
+
+}  // namespace sfc

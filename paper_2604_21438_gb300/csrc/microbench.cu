@@ -1,0 +1,56 @@
+// microbench.cu -- FMA-throughput microbenchmarks used as measured ALU
+// denominators of the roofline (FP64 and FP32 vector pipes).  Each thread
+// runs 8 independent FMA chains in registers; one launch covers every SM
+// several times over.  Not part of the solver.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+template <typename T>
+__global__ void __launch_bounds__(256) fma_chain(T *out, int iters, T a, T b) {
+  T x0 = T(threadIdx.x) * T(1e-3), x1 = x0 + T(1), x2 = x0 + T(2), x3 = x0 + T(3);
+  T x4 = x0 + T(4), x5 = x0 + T(5), x6 = x0 + T(6), x7 = x0 + T(7);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      x0 = x0 * a + b; x1 = x1 * a + b; x2 = x2 * a + b; x3 = x3 * a + b;
+      x4 = x4 * a + b; x5 = x5 * a + b; x6 = x6 * a + b; x7 = x7 * a + b;
+    }
+  }
+  T s = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+  if (s == T(-1.2345)) out[blockIdx.x * blockDim.x + threadIdx.x] = s;   // never true; keeps the chains live
+}
+
+template <typename T>
+static int run(int iters, int blocks_per_sm, double *flops_per_s, float *ms_out) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  const int grid = sms * blocks_per_sm, tpb = 256;
+  T *out = nullptr;
+  if (cudaMalloc(&out, sizeof(T) * grid * tpb) != cudaSuccess) return 1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fma_chain<T><<<grid, tpb>>>(out, iters / 4 + 1, T(0.999999), T(1e-7));   // warm-up
+  cudaEventRecord(e0);
+  fma_chain<T><<<grid, tpb>>>(out, iters, T(0.999999), T(1e-7));
+  cudaEventRecord(e1);
+  cudaError_t err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (err != cudaSuccess) return 1;
+  const double flops = 2.0 * 8.0 * 16.0 * double(iters) * double(grid) * double(tpb);
+  *flops_per_s = flops / (double(ms) * 1e-3);
+  *ms_out = ms;
+  return 0;
+}
+
+extern "C" int sfbench_fma_fp64(int iters, double *flops_per_s, float *ms) {
+  return run<double>(iters, 8, flops_per_s, ms);
+}
+extern "C" int sfbench_fma_fp32(int iters, double *flops_per_s, float *ms) {
+  return run<float>(iters, 8, flops_per_s, ms);
+}

@@ -25,3 +25,4 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+import sys, os; sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))

@@ -1,0 +1,64 @@
+"""Host-side checks of the C ABI: the library loads, exports every entry point
+that include/sfchem.h declares, and rejects bad arguments on the host before
+touching a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2604_21438_gb300 as sf
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "sfchem.h")
+
+
+def declared_functions():
+    txt = open(HDR).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sfchem_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_binding_exports():
+    assert declared_functions() == sorted(sf.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    L = sf.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_default_config_and_validation():
+    L = sf.lib()
+    c = sf.default_config()
+    assert c.f_chem == 0.03 and c.n_cyc == 300 and c.nr_itr_limit == 20 and c.nr_tol == 1e-5
+    assert c.reaction_mask == 0xFFF and c.process_mask == sf.P_ALL and c.flags == 0
+    assert L.sfchem_config_validate(ctypes.byref(c)) == sf.OK
+    bad = [dict(f_chem=0.0), dict(f_chem=1.5), dict(n_cyc=0), dict(gamma_ad=1.0), dict(y_floor=0.0),
+           dict(precision=2), dict(reaction_mask=1 << 12), dict(process_mask=1 << 17), dict(flags=1 << 6),
+           dict(nr_tol=-1.0), dict(Z=float("nan")), dict(reserved=1), dict(n_sub_max=0)]
+    for kw in bad:
+        c = sf.default_config(**kw)
+        assert L.sfchem_config_validate(ctypes.byref(c)) == sf.EINVAL, kw
+    assert L.sfchem_config_validate(None) == sf.EINVAL
+
+
+def test_host_rejections_before_any_launch():
+    L = sf.lib()
+    h = ctypes.c_void_p()
+    bad = sf.default_config(f_chem=-1.0)
+    assert L.sfchem_init(ctypes.byref(bad), ctypes.byref(h)) == sf.EINVAL
+    assert L.sfchem_init(None, None) == sf.EINVAL
+    st, fl = sf.sfchem_state_t(), sf.sfchem_fields_t()
+    assert L.sfchem_step(None, ctypes.byref(st), ctypes.byref(fl), 10, 1.0, 1.0, None) == sf.ENOTINIT
+    assert L.sfchem_stats(None, None) == sf.ENOTINIT
+    assert L.sfchem_finalize(None) == sf.ENOTINIT
+    assert L.sfchem_step_batched(None, None, None, None, None, 0, 1.0, None) == sf.ENOTINIT
+
+
+def test_strerror_and_version():
+    L = sf.lib()
+    for code in range(6):
+        assert L.sfchem_strerror(code)
+    assert L.sfchem_strerror(99) == b"unknown status"
+    assert re.match(rb"\d+\.\d+\.\d+", L.sfchem_version())

@@ -432,3 +432,18 @@ def test_zero_dt_is_identity():
     o = oracle.li_step(c, 0.0, 1.0)
     assert np.all(o["n_sub"] == 0)
     np.testing.assert_array_equal(o["T_g"], c["T_g"])
+
+
+def test_solve5_is_exact_on_badly_scaled_systems():
+    """P10b: the LI systems mix units spanning ~30 decades (condition numbers
+    near 1e16 before scaling).  A = D1 B D2 with B well conditioned and
+    diagonal D1, D2 over 1e-20..1e10: the oracle must recover the known x."""
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        B = rng.standard_normal((5, 5)) + 4 * np.eye(5)
+        d1 = 10.0 ** rng.uniform(-20, 10, 5)
+        d2 = 10.0 ** rng.uniform(-20, 10, 5)
+        A = d1[:, None] * B * d2[None, :]
+        x = rng.standard_normal(5) / d2
+        b = d1 * (B @ (d2 * x))
+        np.testing.assert_allclose(oracle.solve5(A, b), x, rtol=1e-10)
