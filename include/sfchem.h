@@ -90,7 +90,9 @@ enum {
   SFCHEM_F_FREEZE_EIR = 1u << 2, /* hold E_IR fixed */
   SFCHEM_F_FREEZE_YH2 = 1u << 3, /* hold y_H2 fixed */
   SFCHEM_F_FREEZE_YE = 1u << 4,  /* hold y_e fixed */
-  SFCHEM_F_SPLIT = 1u << 5       /* drop the chemistry <-> energy cross-derivatives */
+  SFCHEM_F_SPLIT = 1u << 5,      /* drop the chemistry <-> energy cross-derivatives */
+  SFCHEM_F_REFINE_FF = 1u << 6   /* mixed precision: form the refinement residual with error-free
+                                    FP32 transformations (about 48 bits) instead of FP64 */
 };
 
 /* ------------------------------------------------------------------ types */
@@ -185,7 +187,8 @@ int sfchem_set_config(sfchem_ctx *ctx, const sfchem_config_t *cfg);
 
 /* Advance n_cells cells by dt_seconds each (Sec. 2.2.8) on `stream`
  * (a cudaStream_t; NULL = the legacy default stream).  cd_factor sets
- * C_d = cd_factor * 1e4 erg g^-1 K^-1 (> 0).  n_cells == 0 is a no-op.
+ * C_d = cd_factor * 1e4 erg g^-1 K^-1 (> 0).  n_cells == 0 is a no-op (the
+ * arrays are not read and may be NULL).
  * Pointers must be 8-byte aligned device pointers (state and fields arrays
  * of n_cells entries).  Asynchronous: returns after the launch. */
 int sfchem_step(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_fields_t *fields,

@@ -25,7 +25,7 @@ FP64, MIXED = 0, 1
 OK, EINVAL, ENOTINIT, ECUDA, ETIMEOUT, ENOMEM = 0, 1, 2, 3, 4, 5
 CELL_CAP, CELL_BADINPUT, CELL_NOCONV, CELL_TIGHT, CELL_BADSTEP = 1, 2, 4, 8, 16
 P_ALL = (1 << 17) - 1
-F_FREEZE_TG, F_FREEZE_TD, F_FREEZE_EIR, F_FREEZE_YH2, F_FREEZE_YE, F_SPLIT = 1, 2, 4, 8, 16, 32
+F_FREEZE_TG, F_FREEZE_TD, F_FREEZE_EIR, F_FREEZE_YH2, F_FREEZE_YE, F_SPLIT, F_REFINE_FF = 1, 2, 4, 8, 16, 32, 64
 
 STATE_FIELDS = ("T_g", "T_d", "E_IR", "y_H2", "y_e")            # evolved in place
 INPUT_FIELDS = ("n_H", "G0", "n_EUV", "N_H2")                      # read only

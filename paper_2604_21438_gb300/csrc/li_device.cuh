@@ -62,7 +62,7 @@ constexpr uint32_t P_L9 = 1u << 8, P_L10 = 1u << 9, P_L11 = 1u << 10, P_L12 = 1u
 constexpr uint32_t P_L13 = 1u << 12, P_GG = 1u << 13, P_UV = 1u << 14, P_EMIT = 1u << 15,
                    P_IRABS = 1u << 16;
 constexpr uint32_t F_FTG = 1u << 0, F_FTD = 1u << 1, F_FE = 1u << 2, F_FY2 = 1u << 3,
-                   F_FYE = 1u << 4, F_SPLIT = 1u << 5;
+                   F_FYE = 1u << 4, F_SPLIT = 1u << 5, F_REFINE_FF = 1u << 6;
 constexpr uint8_t ST_CAP = 1, ST_BAD = 2, ST_NOCONV = 4, ST_TIGHT = 8, ST_BADSTEP = 16;
 
 // Solver parameters as the kernels see them.
@@ -95,25 +95,42 @@ __device__ __forceinline__ double fmax_w(double a, double b) { return ::fmax(a, 
 __device__ __forceinline__ float fmax_w(float a, float b) { return ::fmaxf(a, b); }
 
 // ----------------------------------------------------------- per-cell inputs
-// Quantities a cell keeps over one call (FP64).
-struct CellK {
-  double n, rho, fd, Cd, EUV, k9, k10, k11, Gpre, pe, dt_h;
+// Quantities a cell keeps over one call, computed once in FP64 and held in
+// the arithmetic type W of the rates (so the substep loop converts nothing).
+template <typename W> struct CellK {
+  W n, rho, fd, Cd, EUV, k9, k10, k11, Gpre, pe;
+  double dt_h;
 };
 
-__device__ __forceinline__ void make_cellk(CellK &c, double n, double G0, double nEUV, double NH2,
+template <typename W>
+__device__ __forceinline__ void make_cellk(CellK<W> &c, double n, double G0, double nEUV, double NH2,
                                            double cd_factor, double dt_h, const DevCfg &cfg) {
-  c.n = n;
-  c.rho = MUH * MH * n;
-  c.fd = cfg.Z;
-  c.Cd = cd_factor * CD_UNIT;
-  c.EUV = (cfg.pmask & P_UV) ? CLIGHT * (SIG_DUV / (MUH * MH)) * (G0 * U_HAB + nEUV * HNU_EUV) : 0.0;
-  c.k9 = ((cfg.rmask >> 9) & 1u) ? CLIGHT * SIG_EUV * nEUV : 0.0;
-  double fsh = NH2 > NSH0 ? ::exp(-SH_POW * ::log(NH2 / NSH0)) : 1.0;
-  c.k10 = ((cfg.rmask >> 10) & 1u) ? K_LW * G0 * fsh : 0.0;
-  c.k11 = ((cfg.rmask >> 11) & 1u) ? ZETA_CR : 0.0;
-  c.Gpre = (cfg.pmask & P_GG) ? RG * n / ::sqrt(THIGH) : 0.0;
-  c.pe = (cfg.pmask & P_G4) ? PE_K * G0 * cfg.Z : 0.0;
+  c.n = W(n);
+  c.rho = W(MUH * MH * n);
+  c.fd = W(cfg.Z);
+  c.Cd = W(cd_factor * CD_UNIT);
+  c.EUV = (cfg.pmask & P_UV) ? W(CLIGHT * (SIG_DUV / (MUH * MH)) * (G0 * U_HAB + nEUV * HNU_EUV)) : W(0);
+  c.k9 = ((cfg.rmask >> 9) & 1u) ? W(CLIGHT * SIG_EUV * nEUV) : W(0);
+  const double fsh = NH2 > NSH0 ? ::exp(-SH_POW * ::log(NH2 / NSH0)) : 1.0;
+  c.k10 = ((cfg.rmask >> 10) & 1u) ? W(K_LW * G0 * fsh) : W(0);
+  c.k11 = ((cfg.rmask >> 11) & 1u) ? W(ZETA_CR) : W(0);
+  c.Gpre = (cfg.pmask & P_GG) ? W(RG * n / ::sqrt(THIGH)) : W(0);
+  c.pe = (cfg.pmask & P_G4) ? W(PE_K * G0 * cfg.Z) : W(0);
   c.dt_h = dt_h;
+}
+
+// Solver parameters in the arithmetic type W.
+template <typename W> struct CfgW {
+  W f_chem, y_floor, gm1, nr_tol, ncyc_fchem;
+};
+template <typename W> __device__ __forceinline__ CfgW<W> make_cfgw(const DevCfg &d) {
+  CfgW<W> w;
+  w.f_chem = W(d.f_chem);
+  w.y_floor = W(d.y_floor);
+  w.gm1 = W(d.gamma_ad - 1.0);
+  w.nr_tol = W(d.nr_tol);
+  w.ncyc_fchem = W(double(d.n_cyc) * d.f_chem);
+  return w;
 }
 
 // ------------------------------------------------- Table 3 rate coefficients
@@ -123,7 +140,7 @@ template <typename W> struct Rates {
 };
 
 template <typename W>
-__device__ __forceinline__ void eval_rates(W T, W Td, const CellK &c, uint32_t rmask, Rates<W> &r) {
+__device__ __forceinline__ void eval_rates(W T, W Td, const CellK<W> &c, uint32_t rmask, Rates<W> &r) {
   typedef M<W> m;
   const W lnT = m::log(T);
   const W rT = m::rcp(T);
@@ -177,7 +194,7 @@ __device__ __forceinline__ void eval_rates(W T, W Td, const CellK &c, uint32_t r
   {
     const W L = (lnT - W(9.210340371976184)) * W(0.4342944819032518);     // log10(T/1e4)
     const W ncr = m::exp(W(2.302585092994046) * (W(4.845) - W(1.3) * L + W(1.62) * L * L));
-    const W a = W(1) / (W(1) + W(c.n) / ncr);
+    const W a = W(1) / (W(1) + c.n / ncr);
     const W ln_klow = W(-22.860336491462885) - W(6.95e4) * rT;  // ln 1.18e-10
     const W x = W(6000.0) * rT;
     const W em = m::exp(-x);
@@ -198,14 +215,14 @@ __device__ __forceinline__ void eval_rates(W T, W Td, const CellK &c, uint32_t r
     const W ez = m::exp(W(750.0) * (W(1.0 / 75.0) - m::rcp(Td)));
     const W fa = W(1) / (W(1) + ez);
     const W om = ez * fa;                                         // 1 - f_a
-    const W k8 = W(6e-17) * m::sqrt(T * W(1.0 / 300.0)) * fa * W(c.fd) / B;
+    const W k8 = W(6e-17) * m::sqrt(T * W(1.0 / 300.0)) * fa * c.fd / B;
     r.k[8] = k8;
     r.kT[8] = k8 * (W(0.5) - T * (W(0.02) / s + W(2e-3) + W(1.6e-5) * T) / B);
     r.k8d = k8 * (-om * W(750.0) / Td - Td * W(0.02) / (s * B));
   }
-  r.k[9] = W(c.k9); r.kT[9] = W(0);
-  r.k[10] = W(c.k10); r.kT[10] = W(0);
-  r.k[11] = W(c.k11); r.kT[11] = W(0);
+  r.k[9] = c.k9; r.kT[9] = W(0);
+  r.k[10] = c.k10; r.kT[10] = W(0);
+  r.k[11] = c.k11; r.kT[11] = W(0);
 #pragma unroll
   for (int i = 0; i < 9; ++i)
     if (!((rmask >> i) & 1u)) { r.k[i] = W(0); r.kT[i] = W(0); }
@@ -247,11 +264,11 @@ __device__ __forceinline__ W kappa_w(W T, W &beta_emit, W &beta_abs) {
 }
 
 template <typename W>
-__device__ __forceinline__ void eval_system(const double u[5], const CellK &c, const DevCfg &cfg,
-                                            Sys<W> &S) {
+__device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c, const DevCfg &cfg,
+                                            const CfgW<W> &cw, Sys<W> &S) {
   typedef M<W> m;
   const W y2 = W(u[0]), ye = W(u[1]), T = W(u[2]), Td = W(u[3]), E = W(u[4]);
-  const W n = W(c.n);
+  const W n = c.n;
   const uint32_t pm = cfg.pmask, fl = cfg.flags;
   Rates<W> r;
   eval_rates<W>(T, Td, c, cfg.rmask, r);
@@ -327,7 +344,7 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK &c, c
   }
   if (pm & P_G2) SFC_TERM(W(EPI_K) * r.k[9], W(0), yH, W(-2), W(-1));
   if (pm & P_G3) SFC_TERM(W(EPD_K) * r.k[10], W(0), y2, W(1), W(0));
-  if (pm & P_G4) { H += W(c.pe); }
+  if (pm & P_G4) { H += c.pe; }
   if (pm & P_L5) SFC_TERM(W(-13.6 * EV_K) * r.k[0] * n, W(-13.6 * EV_K) * r.kT[0] * n, yH * ye,
                           W(-2) * ye, yH - ye);
   if (pm & P_L6) {
@@ -368,7 +385,7 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK &c, c
     SFC_TERM(b * (T - W(TCMB)), b * T, ye, W(0), W(1));
   }
   if (pm & P_L13) {
-    const W fd = W(c.fd);
+    const W fd = c.fd;
     const W wC = W(GC) * m::exp(W(-TC_S) / T), cC = W(NCRC) / n;
     const W wO = W(GO) * m::exp(W(-TO_S) / T), cO = W(NCRO) / n;
     const W KC = W(XC * TC_S * AC) * fd, KO = W(XO * TO_S * AO) * fd;
@@ -390,12 +407,12 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK &c, c
   const W irabs = on_abs ? ki * W(CRED) * E : W(0);
   const W beta_d = on_emit ? be_d : W(0);
   const W beta_IR = on_abs ? ba_i : W(0);
-  const W G = W(c.Gpre) * m::sqrt(T);
+  const W G = c.Gpre * m::sqrt(T);
   const W gam = W(1) - W(0.8) * m::exp(W(-TLOW) / T);
   const W rr = dTdg / T;                                         // T_d/T_g - 1
   const W zeta = gam * W(0.5) * rr + (gam - W(1)) * W(TLOW) / T * rr - gam;
   const W gg = G * gam * dTdg;                                   // R_g n sqrt(T/T_high) gamma_d (T_d - T_g)
-  const W fd = W(c.fd);
+  const W fd = c.fd;
   // gas-grain transfer in the gas row (Eq. ap_eq:Tg, the gamma_d and zeta terms of Eq. ap_eq:Tg_2)
   const W Hgg = W(KGG) * fd * gg;
   H += Hgg;
@@ -403,7 +420,7 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK &c, c
   const W Hgg_d = W(KGG) * fd * G * gam * Td;
   // scale of the gas row: hs = (gamma_ad - 1) / (ntot/n_H T_g), fixed over the substep
   const W ytot = W(1) - y2 + ye + W(YHE);
-  const W hs = W(cfg.gamma_ad - 1.0) / (ytot * T);
+  const W hs = cw.gm1 / (ytot * T);
   S.F[2] = hs * H;
   S.J[2][0] = hs * H0;
   S.J[2][1] = hs * H1;
@@ -411,16 +428,16 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK &c, c
   S.J[2][3] = hs * (H3h + Hgg_d);
   S.J[2][4] = W(0);
   // dust row (Eq. ap_eq:Td2) scaled by C_d T_d
-  const W Cd = W(c.Cd);
+  const W Cd = c.Cd;
   const W inv_cdtd = m::rcp(Cd * Td);
-  S.F[3] = (irabs + W(c.EUV) - emit - gg) * inv_cdtd;
+  S.F[3] = (irabs + c.EUV - emit - gg) * inv_cdtd;
   S.J[3][0] = W(0);
   S.J[3][1] = W(0);
   S.J[3][2] = -G * zeta * T * inv_cdtd;
   S.J[3][3] = -(G * gam + acTd3 * beta_d) / Cd;
   S.J[3][4] = W(CRED) * beta_IR * E * inv_cdtd;
   // IR row (Appendix C) scaled by E_IR
-  const W rho = W(c.rho);
+  const W rho = c.rho;
   const W invE = m::rcp(E);
   S.F[4] = rho * fd * (emit - irabs) * invE;
   S.J[4][0] = W(0);
@@ -440,8 +457,8 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK &c, c
   if (!(fl & F_FTG)) rd = fmax_w(rd, m::abs(hs * Hgg));
   if (!(fl & F_FE)) rd = fmax_w(rd, m::abs(S.F[4]));
   W rc = W(0);
-  if (!(fl & F_FY2)) rc = m::abs(S.F[0]) / fmax_w(W(u[0]), W(cfg.y_floor));
-  if (!(fl & F_FYE)) rc = fmax_w(rc, m::abs(S.F[1]) / fmax_w(W(u[1]), W(cfg.y_floor)));
+  if (!(fl & F_FY2)) rc = m::abs(S.F[0]) / fmax_w(y2, cw.y_floor);
+  if (!(fl & F_FYE)) rc = fmax_w(rc, m::abs(S.F[1]) / fmax_w(ye, cw.y_floor));
   S.rate_dust = rd;
   S.rate_chem = rc;
   S.rate_energy = (fl & F_FTG) ? W(0) : m::abs(S.F[2]);

@@ -22,18 +22,19 @@ namespace sfc {
 template <typename W> struct LU5 {
   W a[5][5];
   W inv[5];
-  bool sw[10];
+  uint32_t sw;
 };
 
 template <typename W>
 __device__ __forceinline__ bool lu5_factor(LU5<W> &L) {
   int s = 0;
+  L.sw = 0u;
 #pragma unroll
   for (int col = 0; col < 5; ++col) {
 #pragma unroll
     for (int r = col + 1; r < 5; ++r) {
       const bool ex = M<W>::abs(L.a[r][col]) > M<W>::abs(L.a[col][col]);
-      L.sw[s++] = ex;
+      L.sw |= (ex ? 1u : 0u) << (s++);
 #pragma unroll
       for (int j = col; j < 5; ++j) {
         const W x = L.a[col][j], y = L.a[r][j];
@@ -63,7 +64,7 @@ __device__ __forceinline__ void lu5_solve(const LU5<W> &L, V b[5]) {
   for (int col = 0; col < 5; ++col) {
 #pragma unroll
     for (int r = col + 1; r < 5; ++r) {
-      const bool ex = L.sw[s++];
+      const bool ex = (L.sw >> (s++)) & 1u;
       const V x = b[col], y = b[r];
       b[col] = ex ? y : x;
       b[r] = ex ? x : y;
@@ -94,30 +95,32 @@ __device__ __forceinline__ void project(double u[5]) {
 
 // A Newton correction of the tight-coupling iteration is scaled by one
 // factor so that T_d changes by at most 2x and E_IR by at most 16x.
-__device__ __forceinline__ double damp_factor(double Td, double E, double dTd, double dE) {
-  double lam = 1.0;
-  if (Td + dTd > 2.0 * Td) lam = fmin(lam, Td / dTd);
-  if (Td + dTd < 0.5 * Td) lam = fmin(lam, -0.5 * Td / dTd);
-  if (E + dE > 16.0 * E) lam = fmin(lam, 15.0 * E / dE);
-  if (E + dE < E / 16.0) lam = fmin(lam, -(15.0 / 16.0) * E / dE);
+template <typename W>
+__device__ __forceinline__ W damp_factor(W Td, W E, W dTd, W dE) {
+  W lam = W(1);
+  if (Td + dTd > W(2) * Td) lam = min(lam, Td / dTd);
+  if (Td + dTd < W(0.5) * Td) lam = min(lam, W(-0.5) * Td / dTd);
+  if (E + dE > W(16) * E) lam = min(lam, W(15) * E / dE);
+  if (E + dE < E / W(16)) lam = min(lam, W(-15.0 / 16.0) * E / dE);
   return lam;
 }
 
 // Tight coupling (Sec. 2.2.8): Newton iteration of the backward-Euler
 // residual of the dust row (Eq. ap_eq:dust_temp) and the IR row
-// (Eq. ap_eq:Eir) at the substep's new T_g and abundances.  Returns the
+// (Eq. ap_eq:Eir) at the substep's new T_g and abundances.  The iterate is
+// held in FP64; residuals, Jacobian and corrections in W.  Returns the
 // iteration count, negative when nr_itr_limit was reached.
 template <typename W>
-__device__ __forceinline__ int newton_dust(double u[5], const double u0[5], double dt, const CellK &c,
-                                           const DevCfg &cfg) {
+__device__ __forceinline__ int newton_dust(double u[5], const double u0[5], double dt, const CellK<W> &c,
+                                           const DevCfg &cfg, const CfgW<W> &cw) {
   typedef M<W> m;
   const bool frTd = cfg.flags & F_FTD, frE = cfg.flags & F_FE;
   if (frTd && frE) return 0;
   const uint32_t pm = cfg.pmask;
   const W T = W(u[2]);
-  const W G = W(c.Gpre) * m::sqrt(T);
+  const W G = c.Gpre * m::sqrt(T);
   const W gam = W(1) - W(0.8) * m::exp(W(-TLOW) / T);
-  const W Cd = W(c.Cd), rho = W(c.rho), fd = W(c.fd), dtw = W(dt);
+  const W Cd = c.Cd, rho = c.rho, fd = c.fd, dtw = W(dt);
   bool polish = false;
   for (int it = 1; it <= cfg.nr_itr_limit + 1; ++it) {
     if (it > cfg.nr_itr_limit && !polish) break;
@@ -131,11 +134,11 @@ __device__ __forceinline__ int newton_dust(double u[5], const double u0[5], doub
     const W irabs = (pm & P_IRABS) ? ki * W(CRED) * E : W(0);
     const W beta_d = (pm & P_EMIT) ? be_d : W(0);
     const W beta_IR = (pm & P_IRABS) ? ba_i : W(0);
-    const W D = irabs + W(c.EUV) - emit - G * gam * W(u[3] - u[2]);
+    const W D = irabs + c.EUV - emit - G * gam * W(u[3] - u[2]);
     const W I = rho * fd * (emit - irabs);
     // relative unknowns (dT_d/T_d, dE/E); rows scaled by C_d T_d and E
-    W r0 = W(-(u[3] - u0[3]) / u[3]) + dtw * D / (Cd * Td);
-    W r1 = W(-(u[4] - u0[4]) / u[4]) + dtw * I / E;
+    W r0 = -W(u[3] - u0[3]) / Td + dtw * D / (Cd * Td);
+    W r1 = -W(u[4] - u0[4]) / E + dtw * I / E;
     W J00 = W(1) + dtw * (G * gam + acTd3 * beta_d) / Cd;
     W J01 = -dtw * W(CRED) * beta_IR * E / (Cd * Td);
     W J10 = -dtw * rho * fd * acTd3 * beta_d * Td / E;
@@ -146,24 +149,23 @@ __device__ __forceinline__ int newton_dust(double u[5], const double u0[5], doub
     if (!(m::abs(det) > W(0))) return -it;
     const W x0 = (r0 * J11 - J01 * r1) / det;
     const W x1 = (J00 * r1 - J10 * r0) / det;
-    const double d0 = double(x0) * u[3], d1 = double(x1) * u[4];
-    const double lam = polish ? 1.0 : damp_factor(u[3], u[4], d0, d1);
-    u[3] += lam * d0;
-    u[4] += lam * d1;
-    project(u);
+    const W d0 = x0 * Td, d1 = x1 * E;
+    const W lam = polish ? W(1) : damp_factor<W>(Td, E, d0, d1);
+    u[3] = fmax(u[3] + double(lam * d0), TCMB);
+    u[4] = fmax(u[4] + double(lam * d1), EFLOOR);
     // after the stopping test holds, one more full step (not counted) makes
     // the result independent of where the test happened to pass
     if (polish) return it - 1;
-    if (lam == 1.0 && fabs(d0) <= cfg.nr_tol * u[3] && fabs(d1) <= cfg.nr_tol * u[4]) polish = true;
+    if (lam == W(1) && m::abs(d0) <= cw.nr_tol * W(u[3]) && m::abs(d1) <= cw.nr_tol * W(u[4])) polish = true;
   }
   return -cfg.nr_itr_limit;
 }
 
 // ------------------------------------------------------------- one cell
-struct CellRun {
+template <typename W> struct CellRun {
   double u[5];   // y_H2, y_e, T_g, T_d, E_IR
   double t;      // time advanced so far in this call
-  CellK k;
+  CellK<W> k;
   int32_t nsub, nitr;
   uint8_t st;
   int8_t mode;   // -1 undecided, 0 subcycling, 1 tight coupling
@@ -181,23 +183,46 @@ __device__ __forceinline__ bool valid_input(double n, double Tg, double Td, doub
   return true;
 }
 
+// Residual of the factored FP32 system, r = b - A x, formed to about twice
+// the FP32 precision with error-free transformations (TwoProduct by fma,
+// TwoSum) and rounded once.  Only the structural non-zeros of A are visited.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+__device__ __forceinline__ float residual_ff(float b, const float *a, const float *x, int j0, int j1) {
+  float s = b, c = 0.0f;
+  for (int j = j0; j < j1; ++j) {
+    const float p = -a[j] * x[j];
+    const float pe = fmaf(-a[j], x[j], -p);
+    float t, te;
+    two_sum(s, p, t, te);
+    s = t;
+    c += pe + te;
+  }
+  return s + c;
+}
+
 // One LI substep of Sec. 2.2.8; returns true when the cell is finished.
-// MIXED: W = float for rates, Jacobian and LU, with one FP64 residual
-// refinement of the scaled 5x5 solve.
+// MIXED: W = float for rates, Jacobian and LU, followed by one residual
+// refinement of the 5x5 solve (residual in FP64, or with error-free FP32
+// transformations when F_REFINE_FF is set); the update, the projection and the
+// time accounting stay FP64.
 template <typename W, bool MIXED>
-__device__ __forceinline__ bool li_substep(CellRun &c, const DevCfg &cfg) {
+__device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, const CfgW<W> &cw) {
   Sys<W> S;
-  eval_system<W>(c.u, c.k, cfg, S);
+  eval_system<W>(c.u, c.k, cfg, cw, S);
   const double dt_h = c.k.dt_h;
   if (c.mode < 0) {
     // estimated subcycles dt_hydro / (f_chem dt_dust) against N_cyc, from the start state
-    const bool tight = !(dt_h * double(S.rate_dust) < double(cfg.n_cyc) * cfg.f_chem);
+    const bool tight = !(W(dt_h) * S.rate_dust < cw.ncyc_fchem);
     c.mode = tight ? 1 : 0;
     if (tight) c.st |= ST_TIGHT;
   }
-  double inv = fmax(double(S.rate_chem), double(S.rate_energy));
-  if (c.mode == 0) inv = fmax(inv, double(S.rate_dust));
-  const double dtc = inv > 0.0 ? cfg.f_chem / inv : __longlong_as_double(0x7ff0000000000000LL);
+  W inv = fmax_w(S.rate_chem, S.rate_energy);
+  if (c.mode == 0) inv = fmax_w(inv, S.rate_dust);
+  const double dtc = inv > W(0) ? double(cw.f_chem / inv) : __longlong_as_double(0x7ff0000000000000LL);
   const double rem = dt_h - c.t;
   const bool last = (dtc >= rem) || (rem - dtc <= 1e-12 * dt_h);
   const double dts = last ? rem : dtc;
@@ -212,53 +237,57 @@ __device__ __forceinline__ bool li_substep(CellRun &c, const DevCfg &cfg) {
     for (int j = 0; j < 5; ++j) L.a[i][j] = (i == j ? W(1) : W(0)) - dw * S.J[i][j];
     x[i] = dw * S.F[i];
   }
+  W A[5][5], b[5];
+  if constexpr (MIXED) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      b[i] = x[i];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) A[i][j] = L.a[i][j];
+    }
+  }
   if (!lu5_factor<W>(L)) { c.st |= ST_BADSTEP; return true; }
   lu5_solve<W, W>(L, x);
-  double xd[5];
+  W dx[5] = {W(0), W(0), W(0), W(0), W(0)};
+  if constexpr (MIXED) {
+    // one refinement pass against the factored system (A, b): non-zeros of
+    // A are rows 0-2 x columns 0-3, row 3 x columns 2-4, row 4 x columns 3-4
+    const int j0[5] = {0, 0, 0, 2, 3}, j1[5] = {4, 4, 4, 5, 5};
+    W r[5];
+    if (cfg.flags & F_REFINE_FF) {
 #pragma unroll
-  for (int i = 0; i < 5; ++i) xd[i] = double(x[i]);
-  if (MIXED) {
-    // one FP64 residual-refinement pass: r = dt F - (I - dt J) x, over the
-    // structural non-zeros of J (rows 0-2: columns 0-3; row 3: 2-4; row 4: 3-4)
-    double r[5];
+      for (int i = 0; i < 5; ++i) r[i] = residual_ff(float(b[i]), (const float *)A[i], (const float *)x, j0[i], j1[i]);
+    } else {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      double s = 0.0;
+      for (int i = 0; i < 5; ++i) {
+        double acc = double(b[i]);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) s = fma(double(S.J[i][j]), xd[j], s);
-      r[i] = fma(dts, double(S.F[i]) + s, -xd[i]);
+        for (int j = j0[i]; j < j1[i]; ++j) acc = fma(-double(A[i][j]), double(x[j]), acc);
+        r[i] = W(acc);
+      }
     }
-    {
-      double s = fma(double(S.J[3][2]), xd[2], fma(double(S.J[3][3]), xd[3], double(S.J[3][4]) * xd[4]));
-      r[3] = fma(dts, double(S.F[3]) + s, -xd[3]);
-      s = fma(double(S.J[4][3]), xd[3], double(S.J[4][4]) * xd[4]);
-      r[4] = fma(dts, double(S.F[4]) + s, -xd[4]);
-    }
-    W rw[5];
+    lu5_solve<W, W>(L, r);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) rw[i] = W(r[i]);
-    lu5_solve<W, W>(L, rw);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) xd[i] += double(rw[i]);
+    for (int i = 0; i < 5; ++i) dx[i] = r[i];
   }
   double u0[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) u0[i] = c.u[i];
-  c.u[0] += xd[0];
-  c.u[1] += xd[1];
-  c.u[2] = fma(c.u[2], xd[2], c.u[2]);
-  c.u[3] = fma(c.u[3], xd[3], c.u[3]);
-  c.u[4] = fma(c.u[4], xd[4], c.u[4]);
+  // FP64 update: x holds dy_H2, dy_e, dT_g/T_g, dT_d/T_d, dE/E (plus the refinement)
+  c.u[0] += double(x[0]) + double(dx[0]);
+  c.u[1] += double(x[1]) + double(dx[1]);
+  c.u[2] = fma(c.u[2], double(x[2]) + double(dx[2]), c.u[2]);
+  c.u[3] = fma(c.u[3], double(x[3]) + double(dx[3]), c.u[3]);
+  c.u[4] = fma(c.u[4], double(x[4]) + double(dx[4]), c.u[4]);
   project(c.u);
   if (c.mode == 1) {
     // the iteration starts from the LI update of (T_d, E_IR), limited like a Newton correction
-    const double lam = damp_factor(u0[3], u0[4], c.u[3] - u0[3], c.u[4] - u0[4]);
-    if (lam < 1.0) {
-      c.u[3] = u0[3] + lam * (c.u[3] - u0[3]);
-      c.u[4] = u0[4] + lam * (c.u[4] - u0[4]);
-      project(c.u);
+    const W lam = damp_factor<W>(W(u0[3]), W(u0[4]), W(c.u[3] - u0[3]), W(c.u[4] - u0[4]));
+    if (lam < W(1)) {
+      c.u[3] = fmax(u0[3] + double(lam) * (c.u[3] - u0[3]), TCMB);
+      c.u[4] = fmax(u0[4] + double(lam) * (c.u[4] - u0[4]), EFLOOR);
     }
-    int it = newton_dust<W>(c.u, u0, dts, c.k, cfg);
+    int it = newton_dust<W>(c.u, u0, dts, c.k, cfg, cw);
     if (it < 0) { c.st |= ST_NOCONV; it = -it; }
     c.nitr += it;
   }
@@ -270,14 +299,18 @@ __device__ __forceinline__ bool li_substep(CellRun &c, const DevCfg &cfg) {
 }
 
 // H- abundance from the equilibrium of reactions H2 and H3 (unmasked rates)
-__device__ __forceinline__ double y_hminus(double T, double ye) {
-  const double lnT = log(T);
-  const double k2 = exp(-41.11005943727161 + 0.928 * lnT - T * (1.0 / 16200.0));
-  const double N = exp(0.098493 * lnT) + 0.32852 * exp(0.5561 * lnT) + 2.771e-7 * exp(2.1826 * lnT);
-  const double D = 1.0 + 6.191e-3 * exp(1.0461 * lnT) + 8.9712e-11 * exp(3.0424 * lnT) +
-                   3.2576e-14 * exp(3.7741 * lnT);
-  const double k3 = 1.35e-9 * N / D;
-  return k2 * ye / k3;
+template <typename W>
+__device__ __forceinline__ double y_hminus(double Td, double ye) {
+  typedef M<W> m;
+  const W T = W(Td);
+  const W lnT = m::log(T);
+  const W k2 = m::exp(W(-41.11005943727161) + W(0.928) * lnT - T * W(1.0 / 16200.0));
+  const W N = m::exp(W(0.098493) * lnT) + W(0.32852) * m::exp(W(0.5561) * lnT) +
+              W(2.771e-7) * m::exp(W(2.1826) * lnT);
+  const W D = W(1) + W(6.191e-3) * m::exp(W(1.0461) * lnT) + W(8.9712e-11) * m::exp(W(3.0424) * lnT) +
+              W(3.2576e-14) * m::exp(W(3.7741) * lnT);
+  const W k3 = W(1.35e-9) * N / D;
+  return double(k2 / k3) * ye;
 }
 
 // ------------------------------------------------------------ the kernel
@@ -315,6 +348,7 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const DevCfg cfg = a.cfg;
+  const CfgW<W> cw = make_cfgw<W>(cfg);
   // warp-uniform chunk cursor
   int64_t cpos = 0, cend = 0;
   int32_t cblock = -1;
@@ -322,7 +356,7 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
   bool exhausted = false;
   // lane state
   bool have = false;
-  CellRun c;
+  CellRun<W> c;
   int64_t idx = 0;
   int32_t blk = -1;
   // lane statistics
@@ -370,7 +404,7 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
           if (a.status) a.status[idx] = ST_BAD;
           if (a.nsub) a.nsub[idx] = 0;
         } else {
-          make_cellk(c.k, n, G0, nE, NH2, a.cd_factor, cdt, cfg);
+          make_cellk<W>(c.k, n, G0, nE, NH2, a.cd_factor, cdt, cfg);
           project(c.u);
           have = true;
           if (cdt == 0.0) have = false;   // nothing to integrate: store the projected state
@@ -378,7 +412,7 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
             a.y2[idx] = c.u[0]; a.ye[idx] = c.u[1]; a.Tg[idx] = c.u[2]; a.Td[idx] = c.u[3]; a.E[idx] = c.u[4];
             if (a.yH) a.yH[idx] = 1.0 - 2.0 * c.u[0] - c.u[1];
             if (a.yHp) a.yHp[idx] = c.u[1];
-            if (a.yHm) a.yHm[idx] = y_hminus(c.u[2], c.u[1]);
+            if (a.yHm) a.yHm[idx] = y_hminus<W>(c.u[2], c.u[1]);
             if (a.status) a.status[idx] = 0;
             if (a.nsub) a.nsub[idx] = 0;
           }
@@ -389,11 +423,11 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
     }
     if (!__any_sync(FULL, have)) break;
     if (have) {
-      if (li_substep<W, MIXED>(c, cfg)) {
+      if (li_substep<W, MIXED>(c, cfg, cw)) {
         a.y2[idx] = c.u[0]; a.ye[idx] = c.u[1]; a.Tg[idx] = c.u[2]; a.Td[idx] = c.u[3]; a.E[idx] = c.u[4];
         if (a.yH) a.yH[idx] = 1.0 - 2.0 * c.u[0] - c.u[1];
         if (a.yHp) a.yHp[idx] = c.u[1];
-        if (a.yHm) a.yHm[idx] = y_hminus(c.u[2], c.u[1]);
+        if (a.yHm) a.yHm[idx] = y_hminus<W>(c.u[2], c.u[1]);
         if (a.status) a.status[idx] = c.st;
         if (a.nsub) a.nsub[idx] = c.nsub;
         s_sub += (unsigned long long)c.nsub;

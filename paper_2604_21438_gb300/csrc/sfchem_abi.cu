@@ -220,7 +220,7 @@ int validate_cfg(const sfchem_config_t *c) {
   if (!(std::isfinite(c->gamma_ad) && c->gamma_ad > 1.0)) return SFCHEM_EINVAL;
   if (!(std::isfinite(c->y_floor) && c->y_floor > 0.0)) return SFCHEM_EINVAL;
   if (!(std::isfinite(c->nr_tol) && c->nr_tol > 0.0)) return SFCHEM_EINVAL;
-  if (c->reaction_mask >> 12 || c->process_mask >> 17 || c->flags >> 6 || c->reserved) return SFCHEM_EINVAL;
+  if (c->reaction_mask >> 12 || c->process_mask >> 17 || c->flags >> 7 || c->reserved) return SFCHEM_EINVAL;
   return SFCHEM_OK;
 }
 
@@ -408,8 +408,8 @@ int sfchem_step(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_field
   if (n_cells < 0 || !(std::isfinite(dt_seconds) && dt_seconds >= 0.0) ||
       !(std::isfinite(cd_factor) && cd_factor > 0.0))
     return SFCHEM_EINVAL;
+  if (n_cells == 0) return SFCHEM_OK;   // nothing is read: empty arrays may be NULL
   if (int rc = check_arrays(state, fields)) return rc;
-  if (n_cells == 0) return SFCHEM_OK;
   Shape sh;
   if (int rc = resolve_shape(ctx, sh)) return rc;
   const int64_t n_chunks = (n_cells + sh.chunk - 1) / sh.chunk;

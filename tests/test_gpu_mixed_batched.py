@@ -1,0 +1,121 @@
+"""Mixed-precision path against the FP64 oracle (stated error bound), and
+determinism of the launch paths: the batched persistent kernel, the flat
+kernel, sharded launches on separate streams and replays of the captured
+graph all give bitwise identical cells (cells are independent)."""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from _gpu_helpers import err_summary, run_gpu
+
+pytestmark = pytest.mark.gpu
+YR = inputs.YR
+FIELDS = ("T_g", "T_d", "E_IR", "y_H2", "y_e", "y_H")
+# Stated bound of the mixed path on the harshest inputs (independent random
+# cells spanning 10 K - 1e4 K, 1 - 1e6 cm^-3 and strong UV): relative error
+# (abundances below 1e-6 in units of 1e-6).
+MIXED_MEDIAN, MIXED_P99, MIXED_MAX = 1e-6, 1e-3, 1e-2
+
+
+def check_mixed(got, ref, idx=None):
+    s = err_summary(got, ref, small=1e-6, idx=idx)
+    print({k: (f"{v['max']:.2e}", f"{v['p99']:.2e}", f"{v['median']:.2e}") for k, v in s.items()})
+    for k, v in s.items():
+        assert v["median"] <= MIXED_MEDIAN and v["p99"] <= MIXED_P99 and v["max"] <= MIXED_MAX, (k, v)
+
+
+@pytest.mark.parametrize("refine_ff", [False, True])
+def test_mixed_uniform_4096(refine_ff):
+    cells = inputs.cells_uniform(4096, seed=1001)
+    ref = oracle.li_step(cells, 1e3 * YR, 1.0)
+    got = run_gpu(cells, 1e3 * YR, 1.0, precision="mixed", flags=64 if refine_ff else 0)
+    check_mixed(got, ref)
+    assert np.array_equal(got["status"] & 2, ref["status"] & 2)
+
+
+@pytest.mark.parametrize("cd", [1.0, 1000.0])
+def test_mixed_grf128_sampled(cd):
+    cells = inputs.cells_grf(128, seed=1002)
+    got = run_gpu(cells, 1e3 * YR, cd, precision="mixed")
+    idx = np.random.default_rng(8).choice(len(cells["n_H"]), 2048, replace=False)
+    ref = oracle.li_step(inputs.subset(cells, idx), 1e3 * YR, cd)
+    check_mixed(got, ref, idx=idx)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_flat_and_sharded_are_bitwise_identical(precision):
+    import torch
+    import paper_2604_21438_gb300 as sf
+    cells = inputs.cells_uniform(20000, seed=31)
+    dt = 1e3 * YR
+    flat = run_gpu(cells, dt, 10.0, precision=precision)
+    # batched: ragged blocks, uniform dt
+    off = np.array([0, 1, 512, 700, 4096, 9999, 12000, 20000], np.int64)
+    bat = run_gpu(cells, None, 10.0, precision=precision, batched=(off, np.full(len(off) - 1, dt)))
+    for k in FIELDS + ("n_sub", "status"):
+        assert np.array_equal(flat[k], bat[k]), k
+    # shards on two streams, one context each
+    d = sf.to_device(cells)
+    parts = [(0, 7001), (7001, 20000)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    solvers = [sf.Solver(precision), sf.Solver(precision)]
+    torch.cuda.synchronize()
+    for (a, b), st, sv in zip(parts, streams, solvers):
+        with torch.cuda.stream(st):
+            sv.step({k: v[a:b] for k, v in d.items()}, dt, 10.0, stream=st)
+    torch.cuda.synchronize()
+    got = sf.to_host(d)
+    for k in FIELDS + ("n_sub", "status"):
+        assert np.array_equal(flat[k], got[k]), k
+    for sv in solvers:
+        sv.close()
+
+
+def test_graph_replay_and_cost_order():
+    """The batched call replays its captured graph; the second call runs the
+    blocks in the cost order measured by the first and gives the same cells."""
+    import torch
+    import paper_2604_21438_gb300 as sf
+    cells, off, bdt, lvl = inputs.cells_amr(seed=1004)
+    s = sf.Solver("mixed")
+    d = sf.to_device(cells)
+    pristine = {k: d[k].clone() for k in sf.STATE_FIELDS}
+    outs = []
+    for _ in range(3):
+        for k in sf.STATE_FIELDS:
+            d[k].copy_(pristine[k])
+        s.step_batched(d, off, bdt, 100.0)
+        torch.cuda.synchronize()
+        outs.append(sf.to_host(d))
+    for o in outs[1:]:
+        for k in FIELDS + ("n_sub",):
+            assert np.array_equal(outs[0][k], o[k]), k
+    st = s.stats()
+    assert st["calls"] == 3 and st["cells"] == 3 * len(cells["n_H"])
+    s.close()
+
+
+def test_autotune_keeps_results_and_picks_a_shape():
+    import torch
+    import paper_2604_21438_gb300 as sf
+    cells, off, bdt, lvl = inputs.cells_amr(seed=1004)
+    sub = 600                                         # the first 600 blocks
+    n = int(off[sub])
+    cells = inputs.subset(cells, np.arange(n))
+    off, bdt = off[:sub + 1], bdt[:sub]
+    s = sf.Solver("mixed")
+    d = sf.to_device(cells)
+    before = sf.to_host(d)
+    shape = s.autotune(d, off, bdt, 100.0)
+    after = sf.to_host(d)
+    for k in sf.STATE_FIELDS:
+        assert np.array_equal(before[k], after[k]), k
+    assert shape["threads_per_cta"] in (64, 128, 256) and shape["chunk"] in (32, 64, 128)
+    s.step_batched(d, off, bdt, 100.0)
+    torch.cuda.synchronize()
+    ref = run_gpu(cells, None, 100.0, precision="mixed", batched=(off, bdt))
+    got = sf.to_host(d)
+    for k in FIELDS:
+        assert np.array_equal(ref[k], got[k]), k
+    s.close()
