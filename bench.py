@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--workload", default="gmc256", choices=("gmc256", "grf128", "amr3000", "uniform4096"))
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
+    p.add_argument("--no-ff", action="store_true", help="skip the mixed leg with the FP32 error-free refinement")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (error check, cpu_baseline)")
     p.add_argument("--sample", type=int, default=4096, help="cells checked against the oracle")
@@ -224,6 +225,15 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     out_m = sf.to_host({k: d[k] for k in sf.STATE_FIELDS + ("status", "n_sub")})
     res["mixed"] = dict(ms=ms_m, wall=wall_m, stats=st_m, launch=sm.get_launch())
+    # ---- mixed precision with the error-free FP32 refinement residual
+    out_ff = None
+    if not args.no_ff:
+        sff = sf.Solver("mixed", flags=sf.F_REFINE_FF)
+        sff.set_launch(**sm.get_launch())
+        ms_ff, wall_ff, st_ff = timed_leg(sff, args.steps, args.warmup)
+        out_ff = sf.to_host({k: d[k] for k in sf.STATE_FIELDS + ("status", "n_sub")})
+        res["mixed_ff"] = dict(ms=ms_ff, wall=wall_ff, stats=st_ff)
+        sff.close()
     # ---- plain FP64, batched, same workload
     out_d = None
     if not args.no_fp64:
@@ -274,6 +284,10 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": 2 * args.steps,   # per step: schedule kernel + persistent solver kernel
         "clocks": clk,
     }
+    if "mixed_ff" in res:
+        ms_f_max = allreduce_max(res["mixed_ff"]["ms"], world)
+        line["mixed_ff"] = {"value": total_cells / (ms_f_max * 1e-3), "ms_per_step": ms_f_max,
+                            "note": "refinement residual by error-free FP32 transformations (SFCHEM_F_REFINE_FF)"}
     if "fp64" in res:
         ms_d_max = allreduce_max(res["fp64"]["ms"], world)
         line["fp64"] = {"value": total_cells / (ms_d_max * 1e-3), "ms_per_step": ms_d_max,
@@ -291,7 +305,7 @@ def run_ours(args, rank, world, local_rank):
     # roofline of the dominant kernel (the mixed solver kernel)
     line["roofline"] = roofline(res, clk, n)
     if rank == 0 and not args.no_cpu:
-        line["error_vs_oracle"] = error_vs_oracle(cells, off, bdt, cd, out_m, out_d, args.sample)
+        line["error_vs_oracle"] = error_vs_oracle(cells, off, bdt, cd, out_m, out_d, args.sample, out_ff)
         line["cpu_baseline"] = cpu_baseline(cells, off, bdt, cd, args.cpu_seconds)
     return line
 
@@ -324,7 +338,7 @@ def roofline(res, clk, n_cells):
     return out
 
 
-def error_vs_oracle(cells, off, bdt, cd, out_m, out_d, sample):
+def error_vs_oracle(cells, off, bdt, cd, out_m, out_d, sample, out_ff=None):
     """Mixed and FP64 results against the oracle on a seeded sample of cells."""
     import oracle
     n = len(cells["n_H"])
@@ -333,7 +347,7 @@ def error_vs_oracle(cells, off, bdt, cd, out_m, out_d, sample):
     sub = inputs.subset(cells, idx)
     ref = oracle.li_step(sub, bdt[blk], cd)
     out = {"sample_cells": int(idx.size)}
-    for name, got in (("mixed", out_m), ("fp64", out_d)):
+    for name, got in (("mixed", out_m), ("mixed_ff", out_ff), ("fp64", out_d)):
         if got is None:
             continue
         res = {}

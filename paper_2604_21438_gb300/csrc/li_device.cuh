@@ -99,6 +99,7 @@ __device__ __forceinline__ float fmax_w(float a, float b) { return ::fmaxf(a, b)
 // the arithmetic type W of the rates (so the substep loop converts nothing).
 template <typename W> struct CellK {
   W n, rho, fd, Cd, EUV, k9, k10, k11, Gpre, pe;
+  W lnn, rn, rCd;    // ln n_H, 1/n_H, 1/C_d
   double dt_h;
 };
 
@@ -116,6 +117,9 @@ __device__ __forceinline__ void make_cellk(CellK<W> &c, double n, double G0, dou
   c.k11 = ((cfg.rmask >> 11) & 1u) ? W(ZETA_CR) : W(0);
   c.Gpre = (cfg.pmask & P_GG) ? W(RG * n / ::sqrt(THIGH)) : W(0);
   c.pe = (cfg.pmask & P_G4) ? W(PE_K * G0 * cfg.Z) : W(0);
+  c.lnn = W(::log(n));
+  c.rn = W(1.0 / n);
+  c.rCd = W(1.0 / (cd_factor * CD_UNIT));
   c.dt_h = dt_h;
 }
 
@@ -139,11 +143,16 @@ template <typename W> struct Rates {
   W k[12], kT[12], k8d;
 };
 
+// Powers and reciprocals of T_g and T_d shared by the rate and cooling terms.
+template <typename W> struct Pre {
+  W lnT, rT, sqT, rsqT, rTd;
+};
+
 template <typename W>
-__device__ __forceinline__ void eval_rates(W T, W Td, const CellK<W> &c, uint32_t rmask, Rates<W> &r) {
+__device__ __forceinline__ void eval_rates(W T, W Td, const Pre<W> &q, const CellK<W> &c, uint32_t rmask,
+                                           Rates<W> &r) {
   typedef M<W> m;
-  const W lnT = m::log(T);
-  const W rT = m::rcp(T);
+  const W lnT = q.lnT, rT = q.rT;
   // H0: Abel et al. fit in ln T(eV)
   {
     const W x = lnT - W(9.359148232903149);  // ln(11604.5)
@@ -164,7 +173,7 @@ __device__ __forceinline__ void eval_rates(W T, W Td, const CellK<W> &c, uint32_
     const W X = m::exp(W(0.407) * (W(11.654320855151537) - lnT));      // (115188/T)^0.407
     const W lnk = W(-31.22350007575617) + W(1.5) * (W(12.662275226919286) - lnT) - W(2.242) * m::log1p(X);
     r.k[1] = m::exp(lnk);
-    r.kT[1] = r.k[1] * (W(-1.5) + W(2.242 * 0.407) * X / (W(1) + X));
+    r.kT[1] = r.k[1] * (W(-1.5) + W(2.242 * 0.407) * X * m::rcp(W(1) + X));
   }
   // H2: H- formation
   {
@@ -179,29 +188,30 @@ __device__ __forceinline__ void eval_rates(W T, W Td, const CellK<W> &c, uint32_
     const W NT = W(0.098493) * e1 + W(0.32852 * 0.5561) * e2 + W(2.771e-7 * 2.1826) * e3;
     const W D = W(1) + W(6.191e-3) * e4 + W(8.9712e-11) * e5 + W(3.2576e-14) * e6;
     const W DT = W(6.191e-3 * 1.0461) * e4 + W(8.9712e-11 * 3.0424) * e5 + W(3.2576e-14 * 3.7741) * e6;
-    r.k[3] = W(1.35e-9) * N / D;
-    r.kT[3] = r.k[3] * (NT / N - DT / D);
+    const W rD = m::rcp(D);
+    r.k[3] = W(1.35e-9) * N * rD;
+    r.kT[3] = r.k[3] * (NT * m::rcp(N) - DT * rD);
   }
-  // H5: three-body formation; H6 = H5 / 8
+  // H5: three-body formation (T^-1/4 = sqrt(T^-1/2)); H6 = H5 / 8
   {
-    const W ea = m::exp(W(-0.25) * lnT), eb = m::exp(W(-0.5) * lnT);
+    const W eb = q.rsqT, ea = m::sqrt(q.rsqT);
     r.k[5] = W(6e-32) * ea + W(2e-31) * eb;
     r.kT[5] = W(-0.25 * 6e-32) * ea - W(0.5 * 2e-31) * eb;
     r.k[6] = r.k[5] * W(0.125);
     r.kT[6] = r.kT[5] * W(0.125);
   }
-  // H7: k_high^(1-a) k_low^a; H4 stand-in: the same function
+  // H7: k_high^(1-a) k_low^a with a = 1/(1 + n/n_cr); H4 stand-in: the same function
   {
     const W L = (lnT - W(9.210340371976184)) * W(0.4342944819032518);     // log10(T/1e4)
-    const W ncr = m::exp(W(2.302585092994046) * (W(4.845) - W(1.3) * L + W(1.62) * L * L));
-    const W a = W(1) / (W(1) + c.n / ncr);
+    const W lnncr = W(2.302585092994046) * (W(4.845) - W(1.3) * L + W(1.62) * L * L);
+    const W a = m::rcp(W(1) + m::exp(c.lnn - lnncr));
     const W ln_klow = W(-22.860336491462885) - W(6.95e4) * rT;  // ln 1.18e-10
     const W x = W(6000.0) * rT;
     const W em = m::exp(-x);
     const W ln_khigh = W(-16.325735015736566) - W(0.5) * lnT - W(5.2e4) * rT + m::log1p(-em);  // ln 8.125e-8
     const W lnk = (W(1) - a) * ln_khigh + a * ln_klow;
     const W k7 = m::exp(lnk);
-    const W dkh = W(-0.5) + W(5.2e4) * rT - x * em / (W(1) - em);
+    const W dkh = W(-0.5) + W(5.2e4) * rT - x * em * m::rcp(W(1) - em);
     const W dkl = W(6.95e4) * rT;
     const W da = a * (W(1) - a) * (W(-1.3) + W(3.24) * L);
     const W kT7 = k7 * ((W(1) - a) * dkh + a * dkl + (ln_klow - ln_khigh) * da);
@@ -211,14 +221,16 @@ __device__ __forceinline__ void eval_rates(W T, W Td, const CellK<W> &c, uint32_
   // H8: grain-surface formation
   {
     const W s = m::sqrt(T + Td);
+    const W rs = m::rcp(s);
     const W B = W(1) + W(4e-2) * s + W(2e-3) * T + W(8e-6) * T * T;
-    const W ez = m::exp(W(750.0) * (W(1.0 / 75.0) - m::rcp(Td)));
-    const W fa = W(1) / (W(1) + ez);
+    const W rB = m::rcp(B);
+    const W ez = m::exp(W(750.0) * (W(1.0 / 75.0) - q.rTd));
+    const W fa = m::rcp(W(1) + ez);
     const W om = ez * fa;                                         // 1 - f_a
-    const W k8 = W(6e-17) * m::sqrt(T * W(1.0 / 300.0)) * fa * c.fd / B;
+    const W k8 = W(6e-17 * 0.057735026918962584) * q.sqT * fa * c.fd * rB;   // sqrt(T/300)
     r.k[8] = k8;
-    r.kT[8] = k8 * (W(0.5) - T * (W(0.02) / s + W(2e-3) + W(1.6e-5) * T) / B);
-    r.k8d = k8 * (-om * W(750.0) / Td - Td * W(0.02) / (s * B));
+    r.kT[8] = k8 * (W(0.5) - T * (W(0.02) * rs + W(2e-3) + W(1.6e-5) * T) * rB);
+    r.k8d = k8 * (-om * W(750.0) * q.rTd - Td * W(0.02) * rs * rB);
   }
   r.k[9] = c.k9; r.kT[9] = W(0);
   r.k[10] = c.k10; r.kT[10] = W(0);
@@ -270,8 +282,15 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c
   const W y2 = W(u[0]), ye = W(u[1]), T = W(u[2]), Td = W(u[3]), E = W(u[4]);
   const W n = c.n;
   const uint32_t pm = cfg.pmask, fl = cfg.flags;
+  Pre<W> q;
+  q.lnT = m::log(T);
+  q.rT = m::rcp(T);
+  q.sqT = m::sqrt(T);
+  q.rsqT = m::rcp(q.sqT);
+  q.rTd = m::rcp(Td);
+  const W rT = q.rT;
   Rates<W> r;
-  eval_rates<W>(T, Td, c, cfg.rmask, r);
+  eval_rates<W>(T, Td, q, c, cfg.rmask, r);
   // differences that cancel are taken in FP64 and rounded once: y_H near 0
   // (fully molecular or ionized gas) and T_d - T_g in tight gas-dust coupling
   const W yH = W(1.0 - 2.0 * u[0] - u[1]);
@@ -313,18 +332,19 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c
 #define SFC_TERM(C, CT, P, Py2, Pye) \
   { const W c_ = (C), p_ = (P); H += c_ * p_; H0 += c_ * (Py2); H1 += c_ * (Pye); H2 += (CT) * p_; }
   if (pm & P_G1) {
-    const W q1 = W(400) * m::rcp(T);
+    const W q1 = W(400) * rT;
     const W e1 = m::exp(-q1 * q1);
-    const W e2 = m::exp(W(-12000) / (T + W(1200)));
+    const W r12 = m::rcp(T + W(1200));
+    const W e2 = m::exp(W(-12000) * r12);
     const W Dn = W(1.6) * yH * e1 + W(1.4) * y2 * e2;
     const W Dy2 = W(-3.2) * e1 + W(1.4) * e2, Dye = W(-1.6) * e1;
-    const W DT = W(1.6) * yH * e1 * (W(2) * q1 * q1) + W(1.4) * y2 * e2 * (W(12000) * T / ((T + W(1200)) * (T + W(1200))));
-    const W q = W(1e6) / m::sqrt(T);
-    const W den = n * Dn + q;
-    const W f = n * Dn / den;
-    const W fD = n * q / (den * den);                           // df/dDn
+    const W DT = W(1.6) * yH * e1 * (W(2) * q1 * q1) + W(1.4) * y2 * e2 * (W(12000) * T * r12 * r12);
+    const W qq = W(1e6) * q.rsqT;
+    const W rden = m::rcp(n * Dn + qq);
+    const W f = n * Dn * rden;
+    const W fD = n * qq * rden * rden;                          // df/dDn
     const W fy2 = fD * Dy2, fye = fD * Dye;
-    const W fT = (n * q * DT + W(0.5) * n * Dn * q) / (den * den);   // T df/dT
+    const W fT = (n * qq * DT + W(0.5) * n * Dn * qq) * rden * rden;  // T df/dT
     const W gA = k2v * n * yH * ye;                              // H- channel per n
     const W gAy2 = k2v * n * (W(-2) * ye), gAye = k2v * n * (yH - ye), gAT = k2Tv * n * yH * ye;
     const W gB = r.k[5] * n2 * yH2sq * yH;
@@ -351,7 +371,7 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c
     SFC_TERM(W(-4.48 * EV_K) * r.k[4] * n, W(-4.48 * EV_K) * r.kT[4] * n, y2 * yH, yH - W(2) * y2, -y2);
     SFC_TERM(W(-4.48 * EV_K) * r.k[7] * n, W(-4.48 * EV_K) * r.kT[7] * n, y2 * y2, W(2) * y2, W(0));
   }
-  const W lnT = m::log(T);
+  const W lnT = q.lnT;
   const W L10 = lnT * W(0.4342944819032518);
   if (pm & P_L7) {
     W p = W(5.491e-4);
@@ -364,20 +384,21 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c
     SFC_TERM(C, C * dp, ye * ye, W(0), W(2) * ye);
   }
   if (pm & P_L8) SFC_TERM(-T * k2v * n, -T * (k2v + k2Tv) * n, yH * ye, W(-2) * ye, yH - ye);
-  const W sq5 = m::sqrt(T * W(1e-5));
+  const W sq5 = q.sqT * W(0.0031622776601683794);               // sqrt(T / 1e5)
+  const W r1s = m::rcp(W(1) + sq5);
   if (pm & P_L9) {
-    const W C = W(-7.50e-19 / KB) * n * m::exp(W(-118348) / T) / (W(1) + sq5);
-    SFC_TERM(C, C * (W(118348) / T - W(0.5) * sq5 / (W(1) + sq5)), ye * yH, W(-2) * ye, yH - ye);
+    const W C = W(-7.50e-19 / KB) * n * m::exp(W(-118348) * rT) * r1s;
+    SFC_TERM(C, C * (W(118348) * rT - W(0.5) * sq5 * r1s), ye * yH, W(-2) * ye, yH - ye);
   }
   if (pm & P_L10) {
-    const W C = W(-5.54e-17 / KB * YHE) * n * m::exp(W(-0.397) * lnT - W(473638) / T) / (W(1) + sq5);
-    SFC_TERM(C, C * (W(-0.397) + W(473638) / T - W(0.5) * sq5 / (W(1) + sq5)), ye, W(0), W(1));
+    const W C = W(-5.54e-17 / KB * YHE) * n * m::exp(W(-0.397) * lnT - W(473638) * rT) * r1s;
+    SFC_TERM(C, C * (W(-0.397) + W(473638) * rT - W(0.5) * sq5 * r1s), ye, W(0), W(1));
   }
   if (pm & P_L11) {
     const bool lo = T < W(3.2e5);
     const W gff = lo ? W(0.79464) + W(0.1243) * L10 : W(2.13164) - W(0.1240) * L10;
     const W gT = lo ? W(0.1243 * 0.4342944819032518) : W(-0.1240 * 0.4342944819032518);
-    const W b = W(-1.426e-27 / KB) * n * m::sqrt(T);
+    const W b = W(-1.426e-27 / KB) * n * q.sqT;
     SFC_TERM(b * gff, b * (W(0.5) * gff + gT), ye * ye, W(0), W(2) * ye);
   }
   if (pm & P_L12) {
@@ -386,13 +407,13 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c
   }
   if (pm & P_L13) {
     const W fd = c.fd;
-    const W wC = W(GC) * m::exp(W(-TC_S) / T), cC = W(NCRC) / n;
-    const W wO = W(GO) * m::exp(W(-TO_S) / T), cO = W(NCRO) / n;
+    const W wC = W(GC) * m::exp(W(-TC_S) * rT), cC = W(NCRC) * c.rn;
+    const W wO = W(GO) * m::exp(W(-TO_S) * rT), cO = W(NCRO) * c.rn;
     const W KC = W(XC * TC_S * AC) * fd, KO = W(XO * TO_S * AO) * fd;
-    const W dC = W(1) + wC + cC, dO = W(1) + wO + cO;
-    const W val = -(KC * wC / dC + KO * wO / dO);
-    const W valT = -(KC * wC * (W(TC_S) / T) * (W(1) + cC) / (dC * dC) +
-                     KO * wO * (W(TO_S) / T) * (W(1) + cO) / (dO * dO));
+    const W rC = m::rcp(W(1) + wC + cC), rO = m::rcp(W(1) + wO + cO);
+    const W val = -(KC * wC * rC + KO * wO * rO);
+    const W valT = -(KC * wC * (W(TC_S) * rT) * (W(1) + cC) * rC * rC +
+                     KO * wO * (W(TO_S) * rT) * (W(1) + cO) * rO * rO);
     H += val; H2 += valT;
   }
 #undef SFC_TERM
@@ -407,10 +428,10 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c
   const W irabs = on_abs ? ki * W(CRED) * E : W(0);
   const W beta_d = on_emit ? be_d : W(0);
   const W beta_IR = on_abs ? ba_i : W(0);
-  const W G = c.Gpre * m::sqrt(T);
-  const W gam = W(1) - W(0.8) * m::exp(W(-TLOW) / T);
-  const W rr = dTdg / T;                                         // T_d/T_g - 1
-  const W zeta = gam * W(0.5) * rr + (gam - W(1)) * W(TLOW) / T * rr - gam;
+  const W G = c.Gpre * q.sqT;
+  const W gam = W(1) - W(0.8) * m::exp(W(-TLOW) * rT);
+  const W rr = dTdg * rT;                                        // T_d/T_g - 1
+  const W zeta = gam * W(0.5) * rr + (gam - W(1)) * W(TLOW) * rT * rr - gam;
   const W gg = G * gam * dTdg;                                   // R_g n sqrt(T/T_high) gamma_d (T_d - T_g)
   const W fd = c.fd;
   // gas-grain transfer in the gas row (Eq. ap_eq:Tg, the gamma_d and zeta terms of Eq. ap_eq:Tg_2)
@@ -420,7 +441,7 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c
   const W Hgg_d = W(KGG) * fd * G * gam * Td;
   // scale of the gas row: hs = (gamma_ad - 1) / (ntot/n_H T_g), fixed over the substep
   const W ytot = W(1) - y2 + ye + W(YHE);
-  const W hs = cw.gm1 / (ytot * T);
+  const W hs = cw.gm1 * rT * m::rcp(ytot);
   S.F[2] = hs * H;
   S.J[2][0] = hs * H0;
   S.J[2][1] = hs * H1;
@@ -429,12 +450,12 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c
   S.J[2][4] = W(0);
   // dust row (Eq. ap_eq:Td2) scaled by C_d T_d
   const W Cd = c.Cd;
-  const W inv_cdtd = m::rcp(Cd * Td);
+  const W inv_cdtd = c.rCd * q.rTd;
   S.F[3] = (irabs + c.EUV - emit - gg) * inv_cdtd;
   S.J[3][0] = W(0);
   S.J[3][1] = W(0);
   S.J[3][2] = -G * zeta * T * inv_cdtd;
-  S.J[3][3] = -(G * gam + acTd3 * beta_d) / Cd;
+  S.J[3][3] = -(G * gam + acTd3 * beta_d) * c.rCd;
   S.J[3][4] = W(CRED) * beta_IR * E * inv_cdtd;
   // IR row (Appendix C) scaled by E_IR
   const W rho = c.rho;

@@ -108,8 +108,9 @@ __device__ __forceinline__ W damp_factor(W Td, W E, W dTd, W dE) {
 // Tight coupling (Sec. 2.2.8): Newton iteration of the backward-Euler
 // residual of the dust row (Eq. ap_eq:dust_temp) and the IR row
 // (Eq. ap_eq:Eir) at the substep's new T_g and abundances.  The iterate is
-// held in FP64; residuals, Jacobian and corrections in W.  Returns the
-// iteration count, negative when nr_itr_limit was reached.
+// the FP64 starting point plus corrections accumulated in W, so the loop
+// itself runs in W; the corrections are added to the FP64 state once at the
+// end.  Returns the iteration count, negative when nr_itr_limit was reached.
 template <typename W>
 __device__ __forceinline__ int newton_dust(double u[5], const double u0[5], double dt, const CellK<W> &c,
                                            const DevCfg &cfg, const CfgW<W> &cw) {
@@ -119,12 +120,18 @@ __device__ __forceinline__ int newton_dust(double u[5], const double u0[5], doub
   const uint32_t pm = cfg.pmask;
   const W T = W(u[2]);
   const W G = c.Gpre * m::sqrt(T);
-  const W gam = W(1) - W(0.8) * m::exp(W(-TLOW) / T);
-  const W Cd = c.Cd, rho = c.rho, fd = c.fd, dtw = W(dt);
+  const W gam = W(1) - W(0.8) * m::exp(W(-TLOW) * m::rcp(T));
+  const W rho = c.rho, fd = c.fd, dtw = W(dt);
+  const W Tb = W(u[3]), Eb = W(u[4]);           // starting point
+  const W g3 = W(u[3] - u0[3]), g4 = W(u[4] - u0[4]);   // starting point minus the substep's start
+  const W dTg = W(u[3] - u[2]);                 // T_d - T_g at the starting point
+  W a3 = W(0), a4 = W(0);                       // accumulated corrections
+  int result = -cfg.nr_itr_limit;
   bool polish = false;
   for (int it = 1; it <= cfg.nr_itr_limit + 1; ++it) {
     if (it > cfg.nr_itr_limit && !polish) break;
-    const W Td = W(u[3]), E = W(u[4]);
+    const W Td = Tb + a3, E = Eb + a4;
+    const W rTd = m::rcp(Td), rE = m::rcp(E);
     W be_d, ba_d, be_i, ba_i;
     const W kd = kappa_w<W>(Td, be_d, ba_d);
     const W TIR = m::sqrt(m::sqrt(W(1e-4 / ARAD) * E));
@@ -134,31 +141,33 @@ __device__ __forceinline__ int newton_dust(double u[5], const double u0[5], doub
     const W irabs = (pm & P_IRABS) ? ki * W(CRED) * E : W(0);
     const W beta_d = (pm & P_EMIT) ? be_d : W(0);
     const W beta_IR = (pm & P_IRABS) ? ba_i : W(0);
-    const W D = irabs + c.EUV - emit - G * gam * W(u[3] - u[2]);
+    const W D = irabs + c.EUV - emit - G * gam * (dTg + a3);
     const W I = rho * fd * (emit - irabs);
     // relative unknowns (dT_d/T_d, dE/E); rows scaled by C_d T_d and E
-    W r0 = -W(u[3] - u0[3]) / Td + dtw * D / (Cd * Td);
-    W r1 = -W(u[4] - u0[4]) / E + dtw * I / E;
-    W J00 = W(1) + dtw * (G * gam + acTd3 * beta_d) / Cd;
-    W J01 = -dtw * W(CRED) * beta_IR * E / (Cd * Td);
-    W J10 = -dtw * rho * fd * acTd3 * beta_d * Td / E;
+    W r0 = (-(g3 + a3) + dtw * D * c.rCd) * rTd;
+    W r1 = (-(g4 + a4) + dtw * I) * rE;
+    W J00 = W(1) + dtw * (G * gam + acTd3 * beta_d) * c.rCd;
+    W J01 = -dtw * W(CRED) * beta_IR * E * c.rCd * rTd;
+    W J10 = -dtw * rho * fd * acTd3 * beta_d * Td * rE;
     W J11 = W(1) + dtw * rho * W(CRED) * fd * beta_IR;
     if (frTd) { J00 = W(1); J01 = W(0); r0 = W(0); }
     if (frE) { J10 = W(0); J11 = W(1); r1 = W(0); }
     const W det = J00 * J11 - J01 * J10;
-    if (!(m::abs(det) > W(0))) return -it;
-    const W x0 = (r0 * J11 - J01 * r1) / det;
-    const W x1 = (J00 * r1 - J10 * r0) / det;
-    const W d0 = x0 * Td, d1 = x1 * E;
+    if (!(m::abs(det) > W(0))) { result = -it; break; }
+    const W rdet = m::rcp(det);
+    const W d0 = (r0 * J11 - J01 * r1) * rdet * Td;
+    const W d1 = (J00 * r1 - J10 * r0) * rdet * E;
     const W lam = polish ? W(1) : damp_factor<W>(Td, E, d0, d1);
-    u[3] = fmax(u[3] + double(lam * d0), TCMB);
-    u[4] = fmax(u[4] + double(lam * d1), EFLOOR);
+    a3 = fmax_w(Tb + (a3 + lam * d0), W(TCMB)) - Tb;
+    a4 = fmax_w(Eb + (a4 + lam * d1), W(EFLOOR)) - Eb;
     // after the stopping test holds, one more full step (not counted) makes
     // the result independent of where the test happened to pass
-    if (polish) return it - 1;
-    if (lam == W(1) && m::abs(d0) <= cw.nr_tol * W(u[3]) && m::abs(d1) <= cw.nr_tol * W(u[4])) polish = true;
+    if (polish) { result = it - 1; break; }
+    if (lam == W(1) && m::abs(d0) <= cw.nr_tol * (Tb + a3) && m::abs(d1) <= cw.nr_tol * (Eb + a4)) polish = true;
   }
-  return -cfg.nr_itr_limit;
+  u[3] = fmax(u[3] + double(a3), TCMB);
+  u[4] = fmax(u[4] + double(a4), EFLOOR);
+  return result;
 }
 
 // ------------------------------------------------------------- one cell
@@ -273,12 +282,17 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
   double u0[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) u0[i] = c.u[i];
-  // FP64 update: x holds dy_H2, dy_e, dT_g/T_g, dT_d/T_d, dE/E (plus the refinement)
+  // FP64 update: x holds dy_H2, dy_e, dT_g/T_g, dT_d/T_d, dE/E.  The
+  // abundance increments keep the refinement as a separate FP64 term (they
+  // feed y_H = 1 - 2 y_H2 - y_e, which cancels as the gas turns fully
+  // molecular or ionized); the relative thermal increments are combined in W.
   c.u[0] += double(x[0]) + double(dx[0]);
   c.u[1] += double(x[1]) + double(dx[1]);
-  c.u[2] = fma(c.u[2], double(x[2]) + double(dx[2]), c.u[2]);
-  c.u[3] = fma(c.u[3], double(x[3]) + double(dx[3]), c.u[3]);
-  c.u[4] = fma(c.u[4], double(x[4]) + double(dx[4]), c.u[4]);
+#pragma unroll
+  for (int i = 2; i < 5; ++i) x[i] += dx[i];
+  c.u[2] = fma(c.u[2], double(x[2]), c.u[2]);
+  c.u[3] = fma(c.u[3], double(x[3]), c.u[3]);
+  c.u[4] = fma(c.u[4], double(x[4]), c.u[4]);
   project(c.u);
   if (c.mode == 1) {
     // the iteration starts from the LI update of (T_d, E_IR), limited like a Newton correction
