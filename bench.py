@@ -34,15 +34,20 @@ import inputs  # noqa: E402
 METRIC = "chem+thermal cell-updates/s: mixed/batched vs plain FP64 at stated error"
 YR = inputs.YR
 
-# Algorithmic work per cell-substep of the solver kernels, counted from the
-# FP instructions that the ncu capture of each kernel reports per substep
-# (FMA = 2 flops); see the summaries under profiles/.
+# Algorithmic work per cell-substep of the solver kernels: the FP
+# instructions that ncu counts per launch (FMA = 2 flops, add/mul = 1),
+# divided by the substeps of that launch (GRF 128^3 workload, dt = 1e3 yr,
+# C_d = 1e4); profiles/sfchem_li_{mixed,fp64}_grf128.md.
 WORK_PER_SUBSTEP = {
-    "mixed": {"fp32_flops": None, "fp64_flops": None},
-    "fp64": {"fp32_flops": None, "fp64_flops": None},
+    "mixed": {"fp32_flops": 1470.7, "fp64_flops": 65.3},
+    "fp64": {"fp32_flops": 7.5, "fp64_flops": 2060.8},
 }
-# GB300: 152 SMs; FP32: 128 lanes/SM; FP64: 1.25 TFLOP/s nominal at 2.07 GHz
-# (4 FP64 flops/SM/clock).
+# DRAM bytes per cell of one solver launch (same captures: 249.1 MB for
+# 2,097,152 cells, mixed; 274.9 MB, FP64).
+DRAM_BYTES_PER_CELL = {"mixed": 249.05e6 / 2097152, "fp64": 274.93e6 / 2097152}
+# GB300 ALU peaks from unit counts and the SM clock: 152 SMs; FP32 128
+# lanes/SM (256 flops/clk); FP64 2 DFMA/clk/SM (4 flops/clk) -- the
+# "peak_sustained" of the FP64 pipe that ncu reports, 1.26 TFLOP/s at 2.07 GHz.
 N_SM = 152
 FP32_FLOP_PER_SM_CLK = 256.0
 FP64_FLOP_PER_SM_CLK = 4.0
@@ -303,38 +308,41 @@ def run_ours(args, rank, world, local_rank):
     except Exception as exc:  # the measurement is informational
         line["alu_peaks_microbench_tflops"] = {"error": str(exc)}
     # roofline of the dominant kernel (the mixed solver kernel)
-    line["roofline"] = roofline(res, clk, n)
+    line["roofline"] = roofline(res, clk, n, "mixed")
+    if "fp64" in res:
+        line["roofline_fp64"] = roofline(res, clk, n, "fp64")
     if rank == 0 and not args.no_cpu:
         line["error_vs_oracle"] = error_vs_oracle(cells, off, bdt, cd, out_m, out_d, args.sample, out_ff)
         line["cpu_baseline"] = cpu_baseline(cells, off, bdt, cd, args.cpu_seconds)
     return line
 
 
-def roofline(res, clk, n_cells):
-    """ALU roofline of the mixed solver kernel.  Algorithmic work per
-    cell-substep (WORK_PER_SUBSTEP) x substeps of one launch / kernel time;
-    the peak is the FP pipe the kernel is bound by, from unit counts and the
-    maximum SM clock."""
-    st = res["mixed"]["stats"]
+def roofline(res, clk, n_cells, leg="mixed"):
+    """ALU roofline of a solver kernel: algorithmic FP work per cell-substep
+    (WORK_PER_SUBSTEP) x substeps of one launch / its CUDA-event time.  The
+    reported pipe is the one closest to its peak (FP64 for both kernels:
+    on GB300 the FP64 rate is 1/64 of FP32); the other pipe's fraction is
+    given beside it."""
+    st = res[leg]["stats"]
     subs = st["substeps"] / max(st["calls"], 1)
-    ms = res["mixed"]["ms"]
-    w = WORK_PER_SUBSTEP["mixed"]
-    f_mhz = (clk.get("sm_max_mhz") or 2070.0)
+    ms = res[leg]["ms"]
+    w = WORK_PER_SUBSTEP[leg]
+    f_mhz = clk.get("sm_max_mhz") or 2070.0
     peak64 = N_SM * FP64_FLOP_PER_SM_CLK * f_mhz * 1e6 / 1e12
     peak32 = N_SM * FP32_FLOP_PER_SM_CLK * f_mhz * 1e6 / 1e12
-    out = {"bound": "alu", "unit": "TFLOP/s", "traffic": None,
-           "substeps_per_launch": subs, "kernel_ms": ms}
-    if w["fp64_flops"] is None:
-        out.update(achieved=None, peak=peak64, frac=None, pipe="fp64",
-                   note="per-substep work not yet counted")
-        return out
     a64 = w["fp64_flops"] * subs / (ms * 1e-3) / 1e12
     a32 = w["fp32_flops"] * subs / (ms * 1e-3) / 1e12
-    f64, f32 = a64 / peak64, a32 / peak32
-    if f64 >= f32:
-        out.update(achieved=a64, peak=peak64, frac=f64, pipe="fp64", other={"fp32_frac": f32})
+    out = {"bound": "alu", "unit": "TFLOP/s", "kernel": f"sfchem_li_{leg}",
+           "substeps_per_launch": subs, "kernel_ms": ms,
+           "traffic": DRAM_BYTES_PER_CELL[leg] * n_cells,
+           "traffic_note": "dram bytes of one launch, scaled by cells from the GRF 128^3 capture"}
+    if a64 / peak64 >= a32 / peak32:
+        out.update(achieved=a64, peak=peak64, frac=a64 / peak64, pipe="fp64",
+                   other={"pipe": "fp32", "achieved": a32, "peak": peak32, "frac": a32 / peak32})
     else:
-        out.update(achieved=a32, peak=peak32, frac=f32, pipe="fp32", other={"fp64_frac": f64})
+        out.update(achieved=a32, peak=peak32, frac=a32 / peak32, pipe="fp32",
+                   other={"pipe": "fp64", "achieved": a64, "peak": peak64, "frac": a64 / peak64})
+    out["peak_source"] = "unit counts x max SM clock (recipe); FMA microbenchmark in alu_peaks_microbench_tflops"
     return out
 
 
