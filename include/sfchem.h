@@ -238,6 +238,32 @@ const char *sfchem_strerror(int status);
 /* Text of the last CUDA error seen by the library on this thread. */
 const char *sfchem_last_cuda_error(void);
 
+/* Allocation-free batched step (the paper has no counterpart: it is an
+ * interface for embedding).  For callers that cannot call cudaMalloc -- a
+ * host framework that owns every device allocation and forbids others, or
+ * code that must not grow its device footprint once it is running -- and so
+ * cannot create a context.  Same arguments and results as
+ * sfchem_step_batched with a configuration instead of a context (cfg may be
+ * NULL for the defaults).  It allocates nothing: its scratch (work counter,
+ * statistics, the block tables and the chunk table) is one file-scope
+ * __device__ array of 1,131,264 bytes that every GPU which loads the library
+ * holds until the process exits.
+ * Limits: at most SFCHEM_NOALLOC_MAX_BLOCKS blocks and at most
+ * SFCHEM_NOALLOC_MAX_CHUNKS chunks of 64 cells (a block of s cells takes
+ * ceil(s/64) chunks); larger schedules are refused with SFCHEM_EINVAL before
+ * anything is launched.  The first call on a device looks up the array's
+ * device address (once per device, with that device current) and should come
+ * before any stream capture.  All calls share the one array, which keeps the
+ * previous call's contents (each call clears what must start at zero):
+ * calls whose work overlaps on the GPU race on it, so issue them one after
+ * another (one stream, or synchronised).  Statistics are not reported and
+ * the blocks run in index order (no cost ordering across calls). */
+#define SFCHEM_NOALLOC_MAX_BLOCKS 4096
+#define SFCHEM_NOALLOC_MAX_CHUNKS 65536
+int sfchem_step_batched_noalloc(const sfchem_config_t *cfg, const sfchem_state_t *state,
+                                const sfchem_fields_t *fields, const int64_t *block_offset,
+                                const double *block_dt, int32_t n_blocks, double cd_factor, void *stream);
+
 /* Library version as "major.minor.patch". */
 const char *sfchem_version(void);
 

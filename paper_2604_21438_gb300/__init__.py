@@ -77,7 +77,9 @@ _lib = None
 EXPORTS = ("sfchem_config_default", "sfchem_config_validate", "sfchem_init", "sfchem_set_config",
            "sfchem_step", "sfchem_step_batched", "sfchem_set_launch", "sfchem_get_launch",
            "sfchem_autotune", "sfchem_stats", "sfchem_stats_reset", "sfchem_finalize",
-           "sfchem_strerror", "sfchem_last_cuda_error", "sfchem_version")
+           "sfchem_strerror", "sfchem_last_cuda_error", "sfchem_version", "sfchem_step_batched_noalloc")
+# scratch limits of sfchem_step_batched_noalloc (include/sfchem.h)
+NOALLOC_MAX_BLOCKS, NOALLOC_MAX_CHUNKS = 4096, 65536
 
 
 def lib_path() -> str:
@@ -111,6 +113,8 @@ def lib():
     L.sfchem_get_launch.argtypes = [vp, P(sfchem_launch_t)]
     L.sfchem_autotune.argtypes = [vp, P(sfchem_state_t), P(sfchem_fields_t), P(ctypes.c_int64),
                                   P(ctypes.c_double), i32, dbl, vp]
+    L.sfchem_step_batched_noalloc.argtypes = [P(sfchem_config_t), P(sfchem_state_t), P(sfchem_fields_t),
+                                              P(ctypes.c_int64), P(ctypes.c_double), i32, dbl, vp]
     L.sfchem_stats.argtypes = [vp, P(sfchem_stats_t)]
     L.sfchem_stats_reset.argtypes = [vp]
     L.sfchem_finalize.argtypes = [vp]

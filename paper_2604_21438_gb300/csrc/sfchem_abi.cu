@@ -149,6 +149,19 @@ sfchem_schedule(const int64_t *block_offset, float *block_cost, int32_t n_blocks
   }
 }
 
+namespace sfc {
+cudaError_t launch_schedule(const int64_t *block_offset, float *block_cost, int32_t n_blocks, int32_t chunk,
+                            int64_t *ch_start, int32_t *ch_count, int32_t *ch_block, cudaStream_t s) {
+  const size_t smem = n_blocks <= SCHED_SORT_MAX ? (sizeof(float) + sizeof(int32_t)) * SCHED_SORT_MAX : 0;
+  cudaError_t e = cudaFuncSetAttribute(sfchem_schedule, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((sizeof(float) + sizeof(int32_t)) * SCHED_SORT_MAX));
+  if (e != cudaSuccess) return e;
+  sfchem_schedule<<<1, SCHED_THREADS, smem, s>>>(block_offset, block_cost, n_blocks, chunk, ch_start, ch_count,
+                                                 ch_block);
+  return cudaGetLastError();
+}
+}  // namespace sfc
+
 namespace {
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
