@@ -62,6 +62,9 @@ def parse():
     p.add_argument("--workload", default="gmc256", choices=("gmc256", "grf128", "amr3000", "uniform4096"))
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-ff", action="store_true", help="skip the mixed leg with the FP32 error-free refinement")
+    p.add_argument("--no-nr", action="store_true", help="skip the Newton-Raphson reference leg")
+    p.add_argument("--sweep", action="store_true", help="run the dt x C_d sweep on the GRF 128^3 grid instead")
+    p.add_argument("--sweep-precision", default="fp64", choices=("fp64", "mixed"))
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (error check, cpu_baseline)")
     p.add_argument("--sample", type=int, default=4096, help="cells checked against the oracle")
@@ -248,6 +251,26 @@ def run_ours(args, rank, world, local_rank):
         out_d = sf.to_host({k: d[k] for k in sf.STATE_FIELDS + ("status", "n_sub")})
         res["fp64"] = dict(ms=ms_d, wall=wall_d, stats=st_d, steps=k64, warmup=1, launch=sd.get_launch())
         sd.close()
+    # ---- the Newton-Raphson reference solver (Sec. 2.2.8) on the same workload
+    if not args.no_nr and np.all(bdt == bdt[0]):
+        snr = sf.Solver("fp64", n_sub_max=2000)
+        for _ in range(1):
+            reset()
+            snr.step_nr(d, float(bdt[0]), cd)
+        torch.cuda.synchronize()
+        snr.stats_reset()
+        times = []
+        for _ in range(2):
+            reset()
+            a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            snr.step_nr(d, float(bdt[0]), cd)
+            b0.record(stream)
+            torch.cuda.synchronize()
+            times.append(a0.elapsed_time(b0))
+        stn = snr.stats()
+        res["nr"] = dict(ms=float(np.mean(times)), stats=stn)
+        snr.close()
     # ---- end to end through the public API with host buffers
     host_in = {k: torch.as_tensor(cells[k]).pin_memory() for k in sf.STATE_FIELDS + sf.INPUT_FIELDS}
     host_out = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in sf.STATE_FIELDS}
@@ -293,6 +316,14 @@ def run_ours(args, rank, world, local_rank):
         ms_f_max = allreduce_max(res["mixed_ff"]["ms"], world)
         line["mixed_ff"] = {"value": total_cells / (ms_f_max * 1e-3), "ms_per_step": ms_f_max,
                             "note": "refinement residual by error-free FP32 transformations (SFCHEM_F_REFINE_FF)"}
+    if "nr" in res:
+        ms_n_max = allreduce_max(res["nr"]["ms"], world)
+        stn = res["nr"]["stats"]
+        line["nr_fp64"] = {"value": total_cells / (ms_n_max * 1e-3), "ms_per_step": ms_n_max, "steps": 2,
+                           "warmup": 1, "substeps_per_cell": stn["substeps"] / max(stn["cells"], 1),
+                           "outer_iterations_per_cell": stn["newton_iters"] / max(stn["cells"], 1),
+                           "noconv_cells": stn["noconv_cells"],
+                           "note": "Newton-Raphson backward-Euler reference (sfchem_step_nr), uniform-dt workloads"}
     if "fp64" in res:
         ms_d_max = allreduce_max(res["fp64"]["ms"], world)
         line["fp64"] = {"value": total_cells / (ms_d_max * 1e-3), "ms_per_step": ms_d_max,
@@ -467,9 +498,58 @@ def allreduce_max(x: float, world: int) -> float:
     return float(t.item())
 
 
+def run_sweep(args):
+    """The dt x C_d sweep on the GRF 128^3 grid with the plain FP64 path:
+    substep statistics and the deviation of each output from the
+    cd_factor = 1 result (one JSON line per sweep)."""
+    import torch
+    import paper_2604_21438_gb300 as sf
+    cells = inputs.cells_grf(128, seed=1002)
+    d = sf.to_device(cells)
+    pristine = {k: d[k].clone() for k in sf.STATE_FIELDS}
+    n = len(cells["n_H"])
+    rows = []
+    for dt_yr in (1e2, 1e3, 1e4):
+        base = None
+        for cd in (1.0, 10.0, 100.0, 1000.0):
+            for k in sf.STATE_FIELDS:
+                d[k].copy_(pristine[k])
+            s = sf.Solver(args.sweep_precision)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            s.step(d, dt_yr * YR, cd)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            st = s.stats()
+            s.close()
+            out = sf.to_host({k: d[k] for k in sf.STATE_FIELDS + ("n_sub", "status")})
+            if cd == 1.0:
+                base = out
+            dev = {}
+            for k in ("T_g", "T_d", "y_H2", "y_e"):
+                floor = 1e-6 if k.startswith("y_") else 1e-300
+                e = np.abs(out[k] - base[k]) / np.maximum(np.abs(base[k]), floor)
+                dev[k] = {"max": float(e.max()), "median": float(np.median(e))}
+            ns = out["n_sub"]
+            rows.append({"dt_yr": dt_yr, "cd_factor": cd, "C_d": cd * 1e4, "ms": ms,
+                         "cell_updates_per_s": n / (ms * 1e-3),
+                         "n_sub": {"mean": float(ns.mean()), "p50": float(np.median(ns)),
+                                   "p99": float(np.percentile(ns, 99)), "max": int(ns.max())},
+                         "tight_fraction": st["tight_cells"] / max(st["cells"], 1),
+                         "newton_per_substep": st["newton_iters"] / max(st["substeps"], 1),
+                         "deviation_from_cd1": dev})
+    return {"sweep": "dt x C_d on the GRF 128^3 grid", "precision": args.sweep_precision, "cells": n,
+            "rows": rows}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.sweep:
+        if rank == 0:
+            print(json.dumps(run_sweep(args)))
+        return
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)))

@@ -208,6 +208,18 @@ int sfchem_step_batched(sfchem_ctx *ctx, const sfchem_state_t *state,
                         const double *block_dt, int32_t n_blocks, double cd_factor,
                         void *stream);
 
+/* The Newton-Raphson reference solver of Sec. 2.2.8 (FP64), which the paper
+ * validates the LI method against: backward Euler over dt_seconds by three
+ * nested Newton groups -- T_gas outer with a central-difference derivative,
+ * (T_dust, E_IR), species -- to a relative change of nr_tol (relaxed to 1e-3
+ * after nr_itr_limit/2 outer iterations), with substeps
+ * dt_sub = (dt - t_sub)/2^i on failure (Eq. substep_NRchem).  Same arrays,
+ * masks and flags as sfchem_step (precision is ignored); n_sub counts the
+ * accepted substeps and the statistics' newton_iters the outer iterations.
+ * SFCHEM_CELL_NOCONV marks a cell that gave up.  Asynchronous. */
+int sfchem_step_nr(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_fields_t *fields,
+                   int64_t n_cells, double dt_seconds, double cd_factor, void *stream);
+
 /* Force a launch shape (NULL restores the default / autotuned one). */
 int sfchem_set_launch(sfchem_ctx *ctx, const sfchem_launch_t *launch);
 

@@ -75,7 +75,7 @@ _lib = None
 
 # every entry point declared in include/sfchem.h
 EXPORTS = ("sfchem_config_default", "sfchem_config_validate", "sfchem_init", "sfchem_set_config",
-           "sfchem_step", "sfchem_step_batched", "sfchem_set_launch", "sfchem_get_launch",
+           "sfchem_step", "sfchem_step_nr", "sfchem_step_batched", "sfchem_set_launch", "sfchem_get_launch",
            "sfchem_autotune", "sfchem_stats", "sfchem_stats_reset", "sfchem_finalize",
            "sfchem_strerror", "sfchem_last_cuda_error", "sfchem_version", "sfchem_step_batched_noalloc")
 # scratch limits of sfchem_step_batched_noalloc (include/sfchem.h)
@@ -107,6 +107,7 @@ def lib():
     L.sfchem_init.argtypes = [P(sfchem_config_t), P(vp)]
     L.sfchem_set_config.argtypes = [vp, P(sfchem_config_t)]
     L.sfchem_step.argtypes = [vp, P(sfchem_state_t), P(sfchem_fields_t), i64, dbl, dbl, vp]
+    L.sfchem_step_nr.argtypes = [vp, P(sfchem_state_t), P(sfchem_fields_t), i64, dbl, dbl, vp]
     L.sfchem_step_batched.argtypes = [vp, P(sfchem_state_t), P(sfchem_fields_t), P(ctypes.c_int64),
                                       P(ctypes.c_double), i32, dbl, vp]
     L.sfchem_set_launch.argtypes = [vp, P(sfchem_launch_t)]
@@ -217,6 +218,13 @@ class Solver:
         st, fl = make_structs(cells, n)
         _check(lib().sfchem_step(self.handle, ctypes.byref(st), ctypes.byref(fl), n, float(dt),
                                  float(cd_factor), _stream_handle(stream)), "sfchem_step")
+
+    def step_nr(self, cells: dict, dt: float, cd_factor: float = 1.0, stream=None):
+        """The Newton-Raphson reference solver (FP64) on the same arrays."""
+        n = cells["n_H"].numel()
+        st, fl = make_structs(cells, n)
+        _check(lib().sfchem_step_nr(self.handle, ctypes.byref(st), ctypes.byref(fl), n, float(dt),
+                                    float(cd_factor), _stream_handle(stream)), "sfchem_step_nr")
 
     def step_batched(self, cells: dict, block_offset, block_dt, cd_factor: float = 1.0, stream=None):
         import numpy as np

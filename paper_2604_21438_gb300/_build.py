@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsfchem.so")
 BENCH_LIB = os.path.join(HERE, "libsfbench.so")
-UNITS = ("li_fp64.cu", "li_mixed.cu", "sfchem_abi.cu", "noalloc.cu")
+UNITS = ("li_fp64.cu", "li_mixed.cu", "nr_fp64.cu", "sfchem_abi.cu", "noalloc.cu")
 BENCH_UNITS = ("microbench.cu",)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]

@@ -8,6 +8,8 @@ cudaError_t launch_li_fp64(const KArgs &a, int grid, int tpb, cudaStream_t s);
 cudaError_t launch_li_mixed(const KArgs &a, int grid, int tpb, cudaStream_t s);
 cudaError_t occupancy_li_fp64(int tpb, int *ctas_per_sm);
 cudaError_t occupancy_li_mixed(int tpb, int *ctas_per_sm);
+cudaError_t launch_nr_fp64(const KArgs &a, int grid, int tpb, cudaStream_t s);
+cudaError_t occupancy_nr_fp64(int tpb, int *ctas_per_sm);
 // One-CTA schedule kernel of the batched path (cost order and chunk table).
 cudaError_t launch_schedule(const int64_t *block_offset, float *block_cost, int32_t n_blocks, int32_t chunk,
                             int64_t *ch_start, int32_t *ch_count, int32_t *ch_block, cudaStream_t s);

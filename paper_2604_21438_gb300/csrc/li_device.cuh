@@ -241,6 +241,39 @@ __device__ __forceinline__ void eval_rates(W T, W Td, const Pre<W> &q, const Cel
   if (!((rmask >> 8) & 1u)) r.k8d = W(0);
 }
 
+// ----------------------------------------- reaction rates R_i (Eq. eq_chemq)
+// R_H2 = k2 n yH ye + k5 n^2 yH^3 + k6 n^2 yH^2 y2 + k8 n yH - k4 n yH y2 - k7 n y2^2 - k10 y2
+// R_e  = k0 n yH ye + (k9 + k11) yH - k1 n ye^2
+// (H- in equilibrium between reactions H2 and H3: the H- channel forms H2 at
+// k2 n yH ye and returns the electron; yH = 1 - 2 y2 - ye, y_H+ = ye.)
+// J0/J1: d/dy2, d/dye, T d/dT, Td d/dTd (the last two only when withT).
+template <typename W>
+__device__ __forceinline__ void chem_rows(const Rates<W> &r, W n, W y2, W ye, W yH, bool via_on, W &F0, W &F1,
+                                          W J0[4], W J1[4], bool withT) {
+  const W k2v = via_on ? r.k[2] : W(0), k2Tv = via_on ? r.kT[2] : W(0);
+  const W n2 = n * n;
+  const W yH2sq = yH * yH;
+  const W g1 = k2v * n, g5 = r.k[5] * n2, g6 = r.k[6] * n2, g8 = r.k[8] * n, g4 = r.k[4] * n,
+          g7 = r.k[7] * n;
+  F0 = g1 * yH * ye + g5 * yH2sq * yH + g6 * yH2sq * y2 + g8 * yH - g4 * yH * y2 - g7 * y2 * y2 - r.k[10] * y2;
+  // d/dy2 (dyH/dy2 = -2)
+  J0[0] = W(-2) * g1 * ye - W(6) * g5 * yH2sq + g6 * (yH2sq - W(4) * yH * y2) - W(2) * g8 -
+          g4 * (yH - W(2) * y2) - W(2) * g7 * y2 - r.k[10];
+  // d/dye (dyH/dye = -1)
+  J0[1] = g1 * (yH - ye) - W(3) * g5 * yH2sq - W(2) * g6 * yH * y2 - g8 + g4 * y2;
+  const W g0 = r.k[0] * n, g1r = r.k[1] * n, gp = r.k[9] + r.k[11];
+  F1 = g0 * yH * ye + gp * yH - g1r * ye * ye;
+  J1[0] = W(-2) * (g0 * ye + gp);
+  J1[1] = g0 * (yH - ye) - gp - W(2) * g1r * ye;
+  if (withT) {
+    J0[2] = (k2Tv * n) * yH * ye + (r.kT[5] * n2) * yH2sq * yH + (r.kT[6] * n2) * yH2sq * y2 +
+            (r.kT[8] * n) * yH - (r.kT[4] * n) * yH * y2 - (r.kT[7] * n) * y2 * y2;
+    J0[3] = (r.k8d * n) * yH;
+    J1[2] = (r.kT[0] * n) * yH * ye - (r.kT[1] * n) * ye * ye;
+    J1[3] = W(0);
+  }
+}
+
 // --------------------------------------------------------- scaled system
 // F[i]: scaled right-hand side (s^-1); J[i][j]: scaled Jacobian (s^-1),
 // entry (i, j) = (dF_i/du_j) c_j / r_i.  rate_dust / rate_chem / rate_energy:
@@ -250,6 +283,9 @@ template <typename W> struct Sys {
   W J[5][5];
   W F[5];
   W rate_dust, rate_chem, rate_energy;
+  W H;   // (Gamma - Lambda) / (n_H k_B), gas-grain transfer included, unscaled
+  W uf[5];   // the state as seen by this evaluation (rounded to W)
+  W dTdg;    // T_d - T_g, formed in FP64 and rounded to W
 };
 
 __device__ __forceinline__ double kappa_d(double T) {
@@ -280,6 +316,7 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c
                                             const CfgW<W> &cw, Sys<W> &S) {
   typedef M<W> m;
   const W y2 = W(u[0]), ye = W(u[1]), T = W(u[2]), Td = W(u[3]), E = W(u[4]);
+  S.uf[0] = y2; S.uf[1] = ye; S.uf[2] = T; S.uf[3] = Td; S.uf[4] = E;
   const W n = c.n;
   const uint32_t pm = cfg.pmask, fl = cfg.flags;
   Pre<W> q;
@@ -295,34 +332,21 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c
   // (fully molecular or ionized gas) and T_d - T_g in tight gas-dust coupling
   const W yH = W(1.0 - 2.0 * u[0] - u[1]);
   const W dTdg = W(u[3] - u[2]);
+  S.dTdg = dTdg;
   const bool via_on = ((cfg.rmask >> 2) & 1u) && ((cfg.rmask >> 3) & 1u);
 
   // ---- chemistry rows (Eq. eq_deq): R and partials
-  // R_H2 = k2 n yH ye + k5 n^2 yH^3 + k6 n^2 yH^2 y2 + k8 n yH - k4 n yH y2 - k7 n y2^2 - k10 y2
-  // R_e  = k0 n yH ye + (k9 + k11) yH - k1 n ye^2
   const W k2v = via_on ? r.k[2] : W(0), k2Tv = via_on ? r.kT[2] : W(0);
   const W n2 = n * n;
   const W yH2sq = yH * yH;
   {
-    const W g1 = k2v * n, g5 = r.k[5] * n2, g6 = r.k[6] * n2, g8 = r.k[8] * n, g4 = r.k[4] * n,
-            g7 = r.k[7] * n;
-    S.F[0] = g1 * yH * ye + g5 * yH2sq * yH + g6 * yH2sq * y2 + g8 * yH - g4 * yH * y2 - g7 * y2 * y2 -
-             r.k[10] * y2;
-    // d/dy2 (dyH/dy2 = -2)
-    S.J[0][0] = W(-2) * g1 * ye - W(6) * g5 * yH2sq + g6 * (yH2sq - W(4) * yH * y2) - W(2) * g8 -
-                g4 * (yH - W(2) * y2) - W(2) * g7 * y2 - r.k[10];
-    // d/dye (dyH/dye = -1)
-    S.J[0][1] = g1 * (yH - ye) - W(3) * g5 * yH2sq - W(2) * g6 * yH * y2 - g8 + g4 * y2;
-    S.J[0][2] = (k2Tv * n) * yH * ye + (r.kT[5] * n2) * yH2sq * yH + (r.kT[6] * n2) * yH2sq * y2 +
-                (r.kT[8] * n) * yH - (r.kT[4] * n) * yH * y2 - (r.kT[7] * n) * y2 * y2;
-    S.J[0][3] = (r.k8d * n) * yH;
+    W F0, F1, J0[4], J1[4];
+    chem_rows<W>(r, n, y2, ye, yH, via_on, F0, F1, J0, J1, true);
+    S.F[0] = F0;
+    S.F[1] = F1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { S.J[0][j] = J0[j]; S.J[1][j] = J1[j]; }
     S.J[0][4] = W(0);
-    const W g0 = r.k[0] * n, g1r = r.k[1] * n, gp = r.k[9] + r.k[11];
-    S.F[1] = g0 * yH * ye + gp * yH - g1r * ye * ye;
-    S.J[1][0] = W(-2) * (g0 * ye + gp);
-    S.J[1][1] = g0 * (yH - ye) - gp - W(2) * g1r * ye;
-    S.J[1][2] = (r.kT[0] * n) * yH * ye - (r.kT[1] * n) * ye * ye;
-    S.J[1][3] = W(0);
     S.J[1][4] = W(0);
   }
 
@@ -443,6 +467,7 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c
   const W ytot = W(1) - y2 + ye + W(YHE);
   const W hs = cw.gm1 * rT * m::rcp(ytot);
   S.F[2] = hs * H;
+  S.H = H;
   S.J[2][0] = hs * H0;
   S.J[2][1] = hs * H1;
   S.J[2][2] = hs * H2;

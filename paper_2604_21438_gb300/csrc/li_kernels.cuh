@@ -81,6 +81,8 @@ __device__ __forceinline__ void lu5_solve(const LU5<W> &L, V b[5]) {
   }
 }
 
+template <typename W> __device__ __forceinline__ W m_abs(W x) { return M<W>::abs(x); }
+
 // ----------------------------------------------------------- projection
 // Positivity and conservation after an update: 0 <= y_e <= 1,
 // 0 <= y_H2 <= (1 - y_e)/2 (so y_H = 1 - 2 y_H2 - y_e >= 0), temperatures at
@@ -111,20 +113,20 @@ __device__ __forceinline__ W damp_factor(W Td, W E, W dTd, W dE) {
 // the FP64 starting point plus corrections accumulated in W, so the loop
 // itself runs in W; the corrections are added to the FP64 state once at the
 // end.  Returns the iteration count, negative when nr_itr_limit was reached.
+// Inputs in W: T (= T_g, fixed), Tb / Eb (the starting point), g3 / g4 (the
+// starting point minus the substep's start) and dTg (T_d - T_g at the
+// starting point).  The FP64 path forms them exactly from the FP64 state; the
+// mixed path from its W-precision view of the state and the LI increments.
 template <typename W>
-__device__ __forceinline__ int newton_dust(double u[5], const double u0[5], double dt, const CellK<W> &c,
-                                           const DevCfg &cfg, const CfgW<W> &cw) {
+__device__ __forceinline__ int newton_dust_w(double u[5], W T, W Tb, W Eb, W g3, W g4, W dTg, double dt,
+                                             const CellK<W> &c, const DevCfg &cfg, W tol) {
   typedef M<W> m;
   const bool frTd = cfg.flags & F_FTD, frE = cfg.flags & F_FE;
   if (frTd && frE) return 0;
   const uint32_t pm = cfg.pmask;
-  const W T = W(u[2]);
   const W G = c.Gpre * m::sqrt(T);
   const W gam = W(1) - W(0.8) * m::exp(W(-TLOW) * m::rcp(T));
   const W rho = c.rho, fd = c.fd, dtw = W(dt);
-  const W Tb = W(u[3]), Eb = W(u[4]);           // starting point
-  const W g3 = W(u[3] - u0[3]), g4 = W(u[4] - u0[4]);   // starting point minus the substep's start
-  const W dTg = W(u[3] - u[2]);                 // T_d - T_g at the starting point
   W a3 = W(0), a4 = W(0);                       // accumulated corrections
   int result = -cfg.nr_itr_limit;
   bool polish = false;
@@ -163,11 +165,17 @@ __device__ __forceinline__ int newton_dust(double u[5], const double u0[5], doub
     // after the stopping test holds, one more full step (not counted) makes
     // the result independent of where the test happened to pass
     if (polish) { result = it - 1; break; }
-    if (lam == W(1) && m::abs(d0) <= cw.nr_tol * (Tb + a3) && m::abs(d1) <= cw.nr_tol * (Eb + a4)) polish = true;
+    if (lam == W(1) && m::abs(d0) <= tol * (Tb + a3) && m::abs(d1) <= tol * (Eb + a4)) polish = true;
   }
   u[3] = fmax(u[3] + double(a3), TCMB);
   u[4] = fmax(u[4] + double(a4), EFLOOR);
   return result;
+}
+
+// FP64 entry: the starting point is the FP64 state u, the substep's start u0.
+__device__ __forceinline__ int newton_dust(double u[5], const double u0[5], double dt, const CellK<double> &c,
+                                           const DevCfg &cfg, double tol) {
+  return newton_dust_w<double>(u, u[2], u[3], u[4], u[3] - u0[3], u[4] - u0[4], u[3] - u[2], dt, c, cfg, tol);
 }
 
 // ------------------------------------------------------------- one cell
@@ -176,6 +184,7 @@ template <typename W> struct CellRun {
   double t;      // time advanced so far in this call
   CellK<W> k;
   int32_t nsub, nitr;
+  int32_t nri, ntries;   // Newton-Raphson path: halving exponent i and attempts
   uint8_t st;
   int8_t mode;   // -1 undecided, 0 subcycling, 1 tight coupling
 };
@@ -231,7 +240,8 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
   }
   W inv = fmax_w(S.rate_chem, S.rate_energy);
   if (c.mode == 0) inv = fmax_w(inv, S.rate_dust);
-  const double dtc = inv > W(0) ? double(cw.f_chem / inv) : __longlong_as_double(0x7ff0000000000000LL);
+  const W dtcw = cw.f_chem / inv;                   // +inf when every rate vanishes
+  const double dtc = double(dtcw);
   const double rem = dt_h - c.t;
   const bool last = (dtc >= rem) || (rem - dtc <= 1e-12 * dt_h);
   const double dts = last ? rem : dtc;
@@ -239,7 +249,7 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
   // A = I - dt J, b = dt F (scaled rows and columns)
   LU5<W> L;
   W x[5];
-  const W dw = W(dts);
+  const W dw = last ? W(rem) : dtcw;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
 #pragma unroll
@@ -293,15 +303,47 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
   c.u[2] = fma(c.u[2], double(x[2]), c.u[2]);
   c.u[3] = fma(c.u[3], double(x[3]), c.u[3]);
   c.u[4] = fma(c.u[4], double(x[4]), c.u[4]);
-  project(c.u);
+  if constexpr (MIXED) {
+    // The projection only changes a value that reached a bound.  A W-precision
+    // estimate of the new state decides, with a safety margin far above its
+    // rounding error, whether any bound can be active; only then the FP64
+    // projection runs (it is the identity otherwise).
+    const W y2n = S.uf[0] + x[0] + dx[0], yen = S.uf[1] + x[1] + dx[1];
+    const W e2 = W(1e-4) * (m_abs(S.uf[0]) + m_abs(x[0]) + m_abs(dx[0]));
+    const W ee = W(1e-4) * (m_abs(S.uf[1]) + m_abs(x[1]) + m_abs(dx[1]));
+    const bool inside = (y2n > e2) && (yen > ee) && (yen < W(1) - ee - W(1e-6)) &&
+                        (y2n + e2 < (W(1) - yen - ee) * W(0.5) - W(1e-6)) &&
+                        (S.uf[2] * (W(1) + x[2]) > W(TCMB * 1.001)) &&
+                        (S.uf[3] * (W(1) + x[3]) > W(TCMB * 1.001)) &&
+                        (S.uf[4] * (W(1) + x[4]) > W(EFLOOR * 1.001));
+    if (!inside) project(c.u);
+  } else {
+    project(c.u);
+  }
   if (c.mode == 1) {
     // the iteration starts from the LI update of (T_d, E_IR), limited like a Newton correction
-    const W lam = damp_factor<W>(W(u0[3]), W(u0[4]), W(c.u[3] - u0[3]), W(c.u[4] - u0[4]));
-    if (lam < W(1)) {
-      c.u[3] = fmax(u0[3] + double(lam) * (c.u[3] - u0[3]), TCMB);
-      c.u[4] = fmax(u0[4] + double(lam) * (c.u[4] - u0[4]), EFLOOR);
+    int it;
+    if constexpr (MIXED) {
+      // W-precision view of the updated state: the start values plus the LI increments
+      W d3 = S.uf[3] * x[3], d4 = S.uf[4] * x[4];
+      const W lam = damp_factor<W>(S.uf[3], S.uf[4], d3, d4);
+      if (lam < W(1)) {
+        c.u[3] = fmax(u0[3] + double(lam) * (c.u[3] - u0[3]), TCMB);
+        c.u[4] = fmax(u0[4] + double(lam) * (c.u[4] - u0[4]), EFLOOR);
+        d3 = W(c.u[3] - u0[3]);
+        d4 = W(c.u[4] - u0[4]);
+      }
+      const W d2 = S.uf[2] * x[2];
+      it = newton_dust_w<W>(c.u, S.uf[2] + d2, S.uf[3] + d3, S.uf[4] + d4, d3, d4, S.dTdg + (d3 - d2), dts, c.k,
+                            cfg, cw.nr_tol);
+    } else {
+      const double lam = damp_factor<double>(u0[3], u0[4], c.u[3] - u0[3], c.u[4] - u0[4]);
+      if (lam < 1.0) {
+        c.u[3] = fmax(u0[3] + lam * (c.u[3] - u0[3]), TCMB);
+        c.u[4] = fmax(u0[4] + lam * (c.u[4] - u0[4]), EFLOOR);
+      }
+      it = newton_dust(c.u, u0, dts, c.k, cfg, cw.nr_tol);
     }
-    int it = newton_dust<W>(c.u, u0, dts, c.k, cfg, cw);
     if (it < 0) { c.st |= ST_NOCONV; it = -it; }
     c.nitr += it;
   }
@@ -356,7 +398,13 @@ struct KArgs {
   DevCfg cfg;
 };
 
-template <typename W, bool MIXED>
+// Newton-Raphson attempt (nr_device.cuh), used by the NR instantiation.
+__device__ __forceinline__ bool nr_attempt(CellRun<double> &c, const DevCfg &cfg, const CfgW<double> &cw);
+
+// The persistent body.  NR = false: the LI method (Sec. 2.2.8, one substep
+// per loop trip); NR = true: the Newton-Raphson reference (one backward-Euler
+// attempt per loop trip, FP64).
+template <typename W, bool MIXED, bool NR = false>
 __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -407,7 +455,7 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
         const double n = __ldg(a.nH + idx), G0 = __ldg(a.G0 + idx), nE = __ldg(a.nEUV + idx),
                      NH2 = __ldg(a.NH2 + idx);
         c.u[0] = a.y2[idx]; c.u[1] = a.ye[idx]; c.u[2] = a.Tg[idx]; c.u[3] = a.Td[idx]; c.u[4] = a.E[idx];
-        c.t = 0.0; c.nsub = 0; c.nitr = 0; c.st = 0; c.mode = -1;
+        c.t = 0.0; c.nsub = 0; c.nitr = 0; c.nri = 0; c.ntries = 0; c.st = 0; c.mode = -1;
         s_cells++;
         if (!valid_input(n, c.u[2], c.u[3], c.u[4], c.u[0], c.u[1], G0, nE, NH2, cdt)) {
           c.st = ST_BAD;
@@ -437,7 +485,10 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
     }
     if (!__any_sync(FULL, have)) break;
     if (have) {
-      if (li_substep<W, MIXED>(c, cfg, cw)) {
+      bool done;
+      if constexpr (NR) done = nr_attempt(c, cfg, cw);
+      else done = li_substep<W, MIXED>(c, cfg, cw);
+      if (done) {
         a.y2[idx] = c.u[0]; a.ye[idx] = c.u[1]; a.Tg[idx] = c.u[2]; a.Td[idx] = c.u[3]; a.E[idx] = c.u[4];
         if (a.yH) a.yH[idx] = 1.0 - 2.0 * c.u[0] - c.u[1];
         if (a.yHp) a.yHp[idx] = c.u[1];

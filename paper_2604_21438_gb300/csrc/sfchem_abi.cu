@@ -442,6 +442,39 @@ int sfchem_step(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_field
   return SFCHEM_OK;
 }
 
+int sfchem_step_nr(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_fields_t *fields, int64_t n_cells,
+                   double dt_seconds, double cd_factor, void *stream) {
+  if (int rc = check_ctx(ctx)) return rc;
+  if (n_cells < 0 || !(std::isfinite(dt_seconds) && dt_seconds >= 0.0) ||
+      !(std::isfinite(cd_factor) && cd_factor > 0.0))
+    return SFCHEM_EINVAL;
+  if (n_cells == 0) return SFCHEM_OK;
+  if (int rc = check_arrays(state, fields)) return rc;
+  const int tpb = 128;
+  int occ = 0;
+  SFC_CUDA(occupancy_nr_fp64(tpb, &occ));
+  Shape sh;
+  sh.tpb = tpb;
+  sh.ctas_per_sm = occ > 0 ? occ : 1;
+  sh.chunk = 32;
+  sh.grid = ctx->num_sms * sh.ctas_per_sm;
+  const int64_t n_chunks = (n_cells + sh.chunk - 1) / sh.chunk;
+  if (n_chunks > INT32_MAX) return SFCHEM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  KArgs a = base_args(ctx, state, fields, cd_factor);
+  a.n_cells = n_cells;
+  a.dt = dt_seconds;
+  a.chunk = sh.chunk;
+  a.n_chunks = (int32_t)n_chunks;
+  SFC_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), s));
+  SFC_CUDA(cudaEventRecord(ctx->ev0, s));
+  SFC_CUDA(launch_nr_fp64(a, sh.grid, sh.tpb, s));
+  SFC_CUDA(cudaEventRecord(ctx->ev1, s));
+  ctx->timed = true;
+  ctx->calls++;
+  return SFCHEM_OK;
+}
+
 int sfchem_step_batched(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_fields_t *fields,
                         const int64_t *block_offset, const double *block_dt, int32_t n_blocks, double cd_factor,
                         void *stream) {
