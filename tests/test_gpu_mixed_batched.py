@@ -119,3 +119,32 @@ def test_autotune_keeps_results_and_picks_a_shape():
     for k in FIELDS:
         assert np.array_equal(ref[k], got[k]), k
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_gmc256_full_size_in_the_benchmark_launch(precision):
+    """The GMC-like 256^3 grid (16.8M cells) in 16^3 blocks through the
+    batched persistent kernel -- the benchmark's workload and launch -- with a
+    seeded sample of cells checked against the oracle."""
+    cells = inputs.cells_gmc(256, seed=1005)
+    cells, off = inputs.block_major(cells, 256, 16)
+    bdt = np.full(len(off) - 1, 1e3 * YR)
+    got = run_gpu(cells, None, 100.0, precision=precision, batched=(off, bdt))
+    idx = np.sort(np.random.default_rng(17).choice(len(cells["n_H"]), 3000, replace=False))
+    ref = oracle.li_step(inputs.subset(cells, idx), 1e3 * YR, 100.0)
+    if precision == "mixed":
+        check_mixed(got, ref, idx=idx)
+    else:
+        from _gpu_helpers import cell_errors
+        e = cell_errors(got, ref, idx=idx)
+        assert (e <= 1e-9).mean() >= 0.995 and e.max() <= 1e-6, (e.max(), (e <= 1e-9).mean())
+        assert np.array_equal(got["n_sub"][idx], ref["n_sub"])
+
+
+def test_mixed_batched_amr_sampled():
+    cells, off, bdt, lvl = inputs.cells_amr(seed=1004)
+    got = run_gpu(cells, None, 100.0, precision="mixed", batched=(off, bdt))
+    idx = np.sort(np.random.default_rng(12).choice(len(cells["n_H"]), 2048, replace=False))
+    blk = np.searchsorted(off, idx, side="right") - 1
+    ref = oracle.li_step(inputs.subset(cells, idx), bdt[blk], 100.0)
+    check_mixed(got, ref, idx=idx)
