@@ -39,7 +39,7 @@ YR = inputs.YR
 # divided by the substeps of that launch (GRF 128^3 workload, dt = 1e3 yr,
 # C_d = 1e4); profiles/sfchem_li_{mixed,fp64}_grf128.md.
 WORK_PER_SUBSTEP = {
-    "mixed": {"fp32_flops": 1470.7, "fp64_flops": 65.3},
+    "mixed": {"fp32_flops": 1504.9, "fp64_flops": 59.4},
     "fp64": {"fp32_flops": 7.5, "fp64_flops": 2060.8},
 }
 # DRAM bytes per cell of one solver launch (same captures: 249.1 MB for
@@ -246,7 +246,8 @@ def run_ours(args, rank, world, local_rank):
     out_d = None
     if not args.no_fp64:
         sd = sf.Solver("fp64")
-        k64 = max(1, min(args.steps, 2))   # the slow leg: 1 warm-up, 2 timed steps, default launch shape
+        sd.set_launch(64, 0, 32)           # the fastest of the shapes timed on the GRF 128^3 workload
+        k64 = max(1, min(args.steps, 2))   # the slow leg: 1 warm-up, 2 timed steps
         ms_d, wall_d, st_d = timed_leg(sd, k64, 1)
         out_d = sf.to_host({k: d[k] for k in sf.STATE_FIELDS + ("status", "n_sub")})
         res["fp64"] = dict(ms=ms_d, wall=wall_d, stats=st_d, steps=k64, warmup=1, launch=sd.get_launch())

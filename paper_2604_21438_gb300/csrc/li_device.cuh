@@ -91,6 +91,42 @@ template <> struct M<float> {
   static __device__ __forceinline__ float abs(float x) { return ::fabsf(x); }
 };
 
+// ------------------------------------------------ FP32 <-> FP64 conversions
+// On GB300 the FP64 pipe issues 2 instructions per clock per SM against 128
+// FP32/INT lanes, and hardware float<->double conversions run on the FP64
+// pipe.  The mixed path converts often (state in, increments and residuals
+// out), so it converts with integer operations on the exponent and mantissa
+// bits instead.  f2d: exact for normal numbers and zeros; FP32 subnormals
+// (|x| < 1.2e-38) become signed zeros; inf and NaN are kept.  d2f: rounds to
+// nearest (ties away from zero); results below the FP32 normal range become
+// signed zeros, above it signed infinities; NaN stays NaN.
+__device__ __forceinline__ double f2d_int(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t sgn = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  const uint32_t e64 = (e == 0xffu) ? 0x7ffu : e + 896u;            // rebias 127 -> 1023
+  const uint32_t hi = (e == 0u) ? sgn : (sgn | (e64 << 20) | (m >> 3));
+  const uint32_t lo = (e == 0u) ? 0u : (m << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ float d2f_int(double d) {
+  const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+  const uint32_t sgn = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;                   // rebias 1023 -> 127
+  const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  uint32_t bits = (sgn | ((uint32_t)e << 23) | m) + ((lo >> 28) & 1u); // a carry rounds into the exponent
+  const bool special = ((hi >> 20) & 0x7ffu) == 0x7ffu;
+  const bool is_nan = special && (((hi & 0xfffffu) | lo) != 0u);
+  bits = (e <= 0) ? sgn : bits;
+  bits = (e >= 255 || special) ? (sgn | 0x7f800000u) : bits;
+  bits = is_nan ? 0x7fc00000u : bits;
+  return __uint_as_float(bits);
+}
+template <typename W> __device__ __forceinline__ W to_w(double d);
+template <> __device__ __forceinline__ double to_w<double>(double d) { return d; }
+template <> __device__ __forceinline__ float to_w<float>(double d) { return d2f_int(d); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f2d_int(x); }
+
 __device__ __forceinline__ double fmax_w(double a, double b) { return ::fmax(a, b); }
 __device__ __forceinline__ float fmax_w(float a, float b) { return ::fmaxf(a, b); }
 
@@ -315,7 +351,7 @@ template <typename W>
 __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c, const DevCfg &cfg,
                                             const CfgW<W> &cw, Sys<W> &S) {
   typedef M<W> m;
-  const W y2 = W(u[0]), ye = W(u[1]), T = W(u[2]), Td = W(u[3]), E = W(u[4]);
+  const W y2 = to_w<W>(u[0]), ye = to_w<W>(u[1]), T = to_w<W>(u[2]), Td = to_w<W>(u[3]), E = to_w<W>(u[4]);
   S.uf[0] = y2; S.uf[1] = ye; S.uf[2] = T; S.uf[3] = Td; S.uf[4] = E;
   const W n = c.n;
   const uint32_t pm = cfg.pmask, fl = cfg.flags;
@@ -330,8 +366,8 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c
   eval_rates<W>(T, Td, q, c, cfg.rmask, r);
   // differences that cancel are taken in FP64 and rounded once: y_H near 0
   // (fully molecular or ionized gas) and T_d - T_g in tight gas-dust coupling
-  const W yH = W(1.0 - 2.0 * u[0] - u[1]);
-  const W dTdg = W(u[3] - u[2]);
+  const W yH = to_w<W>(1.0 - 2.0 * u[0] - u[1]);
+  const W dTdg = to_w<W>(u[3] - u[2]);
   S.dTdg = dTdg;
   const bool via_on = ((cfg.rmask >> 2) & 1u) && ((cfg.rmask >> 3) & 1u);
 

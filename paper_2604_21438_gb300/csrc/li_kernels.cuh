@@ -167,8 +167,8 @@ __device__ __forceinline__ int newton_dust_w(double u[5], W T, W Tb, W Eb, W g3,
     if (polish) { result = it - 1; break; }
     if (lam == W(1) && m::abs(d0) <= tol * (Tb + a3) && m::abs(d1) <= tol * (Eb + a4)) polish = true;
   }
-  u[3] = fmax(u[3] + double(a3), TCMB);
-  u[4] = fmax(u[4] + double(a4), EFLOOR);
+  u[3] = fmax(u[3] + to_f64(a3), TCMB);
+  u[4] = fmax(u[4] + to_f64(a4), EFLOOR);
   return result;
 }
 
@@ -234,14 +234,14 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
   const double dt_h = c.k.dt_h;
   if (c.mode < 0) {
     // estimated subcycles dt_hydro / (f_chem dt_dust) against N_cyc, from the start state
-    const bool tight = !(W(dt_h) * S.rate_dust < cw.ncyc_fchem);
+    const bool tight = !(to_w<W>(dt_h) * S.rate_dust < cw.ncyc_fchem);
     c.mode = tight ? 1 : 0;
     if (tight) c.st |= ST_TIGHT;
   }
   W inv = fmax_w(S.rate_chem, S.rate_energy);
   if (c.mode == 0) inv = fmax_w(inv, S.rate_dust);
   const W dtcw = cw.f_chem / inv;                   // +inf when every rate vanishes
-  const double dtc = double(dtcw);
+  const double dtc = to_f64(dtcw);
   const double rem = dt_h - c.t;
   const bool last = (dtc >= rem) || (rem - dtc <= 1e-12 * dt_h);
   const double dts = last ? rem : dtc;
@@ -249,7 +249,7 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
   // A = I - dt J, b = dt F (scaled rows and columns)
   LU5<W> L;
   W x[5];
-  const W dw = last ? W(rem) : dtcw;
+  const W dw = last ? to_w<W>(rem) : dtcw;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
 #pragma unroll
@@ -279,10 +279,10 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
     } else {
 #pragma unroll
       for (int i = 0; i < 5; ++i) {
-        double acc = double(b[i]);
+        double acc = to_f64(b[i]);
 #pragma unroll
-        for (int j = j0[i]; j < j1[i]; ++j) acc = fma(-double(A[i][j]), double(x[j]), acc);
-        r[i] = W(acc);
+        for (int j = j0[i]; j < j1[i]; ++j) acc = fma(-to_f64(A[i][j]), to_f64(x[j]), acc);
+        r[i] = to_w<W>(acc);
       }
     }
     lu5_solve<W, W>(L, r);
@@ -296,13 +296,13 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
   // abundance increments keep the refinement as a separate FP64 term (they
   // feed y_H = 1 - 2 y_H2 - y_e, which cancels as the gas turns fully
   // molecular or ionized); the relative thermal increments are combined in W.
-  c.u[0] += double(x[0]) + double(dx[0]);
-  c.u[1] += double(x[1]) + double(dx[1]);
+  c.u[0] += to_f64(x[0]) + to_f64(dx[0]);
+  c.u[1] += to_f64(x[1]) + to_f64(dx[1]);
 #pragma unroll
   for (int i = 2; i < 5; ++i) x[i] += dx[i];
-  c.u[2] = fma(c.u[2], double(x[2]), c.u[2]);
-  c.u[3] = fma(c.u[3], double(x[3]), c.u[3]);
-  c.u[4] = fma(c.u[4], double(x[4]), c.u[4]);
+  c.u[2] = fma(c.u[2], to_f64(x[2]), c.u[2]);
+  c.u[3] = fma(c.u[3], to_f64(x[3]), c.u[3]);
+  c.u[4] = fma(c.u[4], to_f64(x[4]), c.u[4]);
   if constexpr (MIXED) {
     // The projection only changes a value that reached a bound.  A W-precision
     // estimate of the new state decides, with a safety margin far above its
@@ -328,10 +328,10 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
       W d3 = S.uf[3] * x[3], d4 = S.uf[4] * x[4];
       const W lam = damp_factor<W>(S.uf[3], S.uf[4], d3, d4);
       if (lam < W(1)) {
-        c.u[3] = fmax(u0[3] + double(lam) * (c.u[3] - u0[3]), TCMB);
-        c.u[4] = fmax(u0[4] + double(lam) * (c.u[4] - u0[4]), EFLOOR);
-        d3 = W(c.u[3] - u0[3]);
-        d4 = W(c.u[4] - u0[4]);
+        c.u[3] = fmax(u0[3] + to_f64(lam) * (c.u[3] - u0[3]), TCMB);
+        c.u[4] = fmax(u0[4] + to_f64(lam) * (c.u[4] - u0[4]), EFLOOR);
+        d3 = to_w<W>(c.u[3] - u0[3]);
+        d4 = to_w<W>(c.u[4] - u0[4]);
       }
       const W d2 = S.uf[2] * x[2];
       it = newton_dust_w<W>(c.u, S.uf[2] + d2, S.uf[3] + d3, S.uf[4] + d4, d3, d4, S.dTdg + (d3 - d2), dts, c.k,
