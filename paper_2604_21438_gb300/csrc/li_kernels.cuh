@@ -256,14 +256,10 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
     for (int j = 0; j < 5; ++j) L.a[i][j] = (i == j ? W(1) : W(0)) - dw * S.J[i][j];
     x[i] = dw * S.F[i];
   }
-  W A[5][5], b[5];
+  W b[5];
   if constexpr (MIXED) {
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      b[i] = x[i];
-#pragma unroll
-      for (int j = 0; j < 5; ++j) A[i][j] = L.a[i][j];
-    }
+    for (int i = 0; i < 5; ++i) b[i] = x[i];
   }
   if (!lu5_factor<W>(L)) { c.st |= ST_BADSTEP; return true; }
   lu5_solve<W, W>(L, x);
@@ -271,17 +267,24 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
   if constexpr (MIXED) {
     // one refinement pass against the factored system (A, b): non-zeros of
     // A are rows 0-2 x columns 0-3, row 3 x columns 2-4, row 4 x columns 3-4
+    // (A is re-formed from J: the same FP32 operations give the same entries)
     const int j0[5] = {0, 0, 0, 2, 3}, j1[5] = {4, 4, 4, 5, 5};
     W r[5];
     if (cfg.flags & F_REFINE_FF) {
 #pragma unroll
-      for (int i = 0; i < 5; ++i) r[i] = residual_ff(float(b[i]), (const float *)A[i], (const float *)x, j0[i], j1[i]);
+      for (int i = 0; i < 5; ++i) {
+        W Ai[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) Ai[j] = (i == j ? W(1) : W(0)) - dw * S.J[i][j];
+        r[i] = residual_ff(float(b[i]), (const float *)Ai, (const float *)x, j0[i], j1[i]);
+      }
     } else {
 #pragma unroll
       for (int i = 0; i < 5; ++i) {
         double acc = to_f64(b[i]);
 #pragma unroll
-        for (int j = j0[i]; j < j1[i]; ++j) acc = fma(-to_f64(A[i][j]), to_f64(x[j]), acc);
+        for (int j = j0[i]; j < j1[i]; ++j)
+          acc = fma(-to_f64((i == j ? W(1) : W(0)) - dw * S.J[i][j]), to_f64(x[j]), acc);
         r[i] = to_w<W>(acc);
       }
     }
