@@ -554,9 +554,24 @@ LIOut li_cell(double u[5], const CellIn &ci, double dt_h, const oracle_config &c
     else dts = dtc;
     if (!(dts > 0.0) || !std::isfinite(dts)) { o.status |= ORACLE_ST_BADSTEP; break; }
     double A[25], b[5], du[5], u0[5];
-    assemble(s, dts, c, A, b);
     std::memcpy(u0, u, sizeof(u0));
-    if (solve_n(5, A, b, du) != 0) { o.status |= ORACLE_ST_BADSTEP; break; }
+    // reading: the LI step rests on small changes (Delta y_j << y_j in the
+    // derivation of Eq. eq_deq).  An update that changes y_H2 or y_e by more
+    // than half of max(y, y_floor), or T_g by more than a factor 2, lies
+    // outside that regime (a near-singular I - dt J at an unstable balance):
+    // the substep is redone with half the step, at most 30 times.
+    bool bad_solve = false;
+    for (int halvings = 0;; ++halvings) {
+      assemble(s, dts, c, A, b);
+      if (solve_n(5, A, b, du) != 0) { bad_solve = true; break; }
+      bool small = std::fabs(du[0]) <= 0.5 * std::max(u0[0], c.y_floor) &&
+                   std::fabs(du[1]) <= 0.5 * std::max(u0[1], c.y_floor) &&
+                   du[2] <= u0[2] && du[2] >= -0.5 * u0[2];
+      if (small || halvings >= 30) break;
+      dts *= 0.5;
+      last = false;
+    }
+    if (bad_solve) { o.status |= ORACLE_ST_BADSTEP; break; }
     for (int j = 0; j < 5; ++j) u[j] += du[j];
     project(u);
     if (tight) {

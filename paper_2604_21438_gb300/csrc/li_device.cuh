@@ -129,6 +129,12 @@ __device__ __forceinline__ double to_f64(float x) { return f2d_int(x); }
 
 __device__ __forceinline__ double fmax_w(double a, double b) { return ::fmax(a, b); }
 __device__ __forceinline__ float fmax_w(float a, float b) { return ::fmaxf(a, b); }
+// 2^-n for 0 <= n <= 126, built from the exponent field (exact)
+template <typename W> __device__ __forceinline__ W pow2_neg(int n);
+template <> __device__ __forceinline__ double pow2_neg<double>(int n) {
+  return __longlong_as_double((long long)(1023 - n) << 52);
+}
+template <> __device__ __forceinline__ float pow2_neg<float>(int n) { return __int_as_float((127 - n) << 23); }
 
 // ----------------------------------------------------------- per-cell inputs
 // Quantities a cell keeps over one call, computed once in FP64 and held in

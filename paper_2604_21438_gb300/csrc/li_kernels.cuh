@@ -184,7 +184,7 @@ template <typename W> struct CellRun {
   double t;      // time advanced so far in this call
   CellK<W> k;
   int32_t nsub, nitr;
-  int32_t nri, ntries;   // Newton-Raphson path: halving exponent i and attempts
+  int32_t nri, ntries;   // halving exponent of the step (both methods); NR attempts
   uint8_t st;
   int8_t mode;   // -1 undecided, 0 subcycling, 1 tight coupling
 };
@@ -243,13 +243,16 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
   const W dtcw = cw.f_chem / inv;                   // +inf when every rate vanishes
   const double dtc = to_f64(dtcw);
   const double rem = dt_h - c.t;
-  const bool last = (dtc >= rem) || (rem - dtc <= 1e-12 * dt_h);
-  const double dts = last ? rem : dtc;
+  // c.nri > 0: the update of this substep was rejected c.nri times (below)
+  // and is redone with the step halved as often (exact powers of two)
+  const bool fits = (dtc >= rem) || (rem - dtc <= 1e-12 * dt_h);
+  const bool last = fits && c.nri == 0;
+  const double dts = (fits ? rem : dtc) * pow2_neg<double>(c.nri);
   if (!(dts > 0.0) || !isfinite(dts)) { c.st |= ST_BADSTEP; return true; }
   // A = I - dt J, b = dt F (scaled rows and columns)
   LU5<W> L;
   W x[5];
-  const W dw = last ? to_w<W>(rem) : dtcw;
+  const W dw = (fits ? to_w<W>(rem) : dtcw) * pow2_neg<W>(c.nri);
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
 #pragma unroll
@@ -291,6 +294,20 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
     lu5_solve<W, W>(L, r);
 #pragma unroll
     for (int i = 0; i < 5; ++i) dx[i] = r[i];
+  }
+  {
+    // The LI step rests on small changes (Delta y << y in the derivation of
+    // Eq. eq_deq).  An update that moves y_H2 or y_e by more than half of
+    // max(y, y_floor), or T_g by more than a factor 2, is outside that regime
+    // (a nearly singular I - dt J): the substep is taken again with half the
+    // step, at most 30 times.  The retry is a trip of the caller's loop, so
+    // nothing of this system stays live across it; the system is evaluated
+    // again from the same state.
+    const W e0 = x[0] + dx[0], e1 = x[1] + dx[1], e2 = x[2] + dx[2];
+    const bool small = m_abs(e0) <= W(0.5) * fmax_w(S.uf[0], cw.y_floor) &&
+                       m_abs(e1) <= W(0.5) * fmax_w(S.uf[1], cw.y_floor) && e2 <= W(1) && e2 >= W(-0.5);
+    if (!small && c.nri < 30) { c.nri++; return false; }
+    c.nri = 0;
   }
   double u0[5];
 #pragma unroll
