@@ -16,9 +16,14 @@ namespace sfc {
 
 // ------------------------------------------------------------------- 5x5 LU
 // Gaussian elimination with partial pivoting (largest |a| in the column, the
-// first such row on ties).  Row exchanges touch only the active columns, and
-// the multipliers stay where they were computed, so a second right-hand side
-// can be solved by replaying the same exchanges (sw) and eliminations.
+// first such row on ties) on the fixed structure of A = I - dt J: rows 0-2
+// (y_H2, y_e, T_g) have non-zeros in columns 0-3, row 3 (T_d) in columns 2-4,
+// row 4 (E_IR) in columns 3-4.  A structural zero never wins a pivot search
+// and eliminating against it changes nothing, so only the candidate rows and
+// the non-zero columns are visited: the factors are those of the dense
+// elimination.  Row exchanges touch only the active columns, and the
+// multipliers stay where they were computed, so a second right-hand side is
+// solved by replaying the same exchanges (bits of sw) and eliminations.
 template <typename W> struct LU5 {
   W a[5][5];
   W inv[5];
@@ -26,59 +31,84 @@ template <typename W> struct LU5 {
 };
 
 template <typename W>
-__device__ __forceinline__ bool lu5_factor(LU5<W> &L) {
-  int s = 0;
-  L.sw = 0u;
+__device__ __forceinline__ void lu5_swap(LU5<W> &L, int p, int r, int j0, int j1, int bit) {
+  const bool ex = M<W>::abs(L.a[r][p]) > M<W>::abs(L.a[p][p]);
+  L.sw |= (ex ? 1u : 0u) << bit;
 #pragma unroll
-  for (int col = 0; col < 5; ++col) {
-#pragma unroll
-    for (int r = col + 1; r < 5; ++r) {
-      const bool ex = M<W>::abs(L.a[r][col]) > M<W>::abs(L.a[col][col]);
-      L.sw |= (ex ? 1u : 0u) << (s++);
-#pragma unroll
-      for (int j = col; j < 5; ++j) {
-        const W x = L.a[col][j], y = L.a[r][j];
-        L.a[col][j] = ex ? y : x;
-        L.a[r][j] = ex ? x : y;
-      }
-    }
-    const W piv = L.a[col][col];
-    if (!(M<W>::abs(piv) > W(0))) return false;
-    const W ip = W(1) / piv;
-    L.inv[col] = ip;
-#pragma unroll
-    for (int r = col + 1; r < 5; ++r) {
-      const W f = L.a[r][col] * ip;
-      L.a[r][col] = f;
-#pragma unroll
-      for (int j = col + 1; j < 5; ++j) L.a[r][j] -= f * L.a[col][j];
-    }
+  for (int j = j0; j < j1; ++j) {
+    const W x = L.a[p][j], y = L.a[r][j];
+    L.a[p][j] = ex ? y : x;
+    L.a[r][j] = ex ? x : y;
   }
+}
+
+template <typename W>
+__device__ __forceinline__ bool lu5_pivot(LU5<W> &L, int p) {
+  const W piv = L.a[p][p];
+  if (!(M<W>::abs(piv) > W(0))) return false;
+  L.inv[p] = W(1) / piv;
   return true;
+}
+
+template <typename W>
+__device__ __forceinline__ void lu5_elim(LU5<W> &L, int p, int r, int j1) {
+  const W f = L.a[r][p] * L.inv[p];
+  L.a[r][p] = f;
+#pragma unroll
+  for (int j = p + 1; j < j1; ++j) L.a[r][j] -= f * L.a[p][j];
+}
+
+template <typename W>
+__device__ __forceinline__ bool lu5_factor(LU5<W> &L) {
+  L.sw = 0u;
+  // column 0: candidates rows 1, 2 (columns 0-3)
+  lu5_swap(L, 0, 1, 0, 4, 0);
+  lu5_swap(L, 0, 2, 0, 4, 1);
+  if (!lu5_pivot(L, 0)) return false;
+  lu5_elim(L, 0, 1, 4);
+  lu5_elim(L, 0, 2, 4);
+  // column 1: candidate row 2 (columns 1-3)
+  lu5_swap(L, 1, 2, 1, 4, 2);
+  if (!lu5_pivot(L, 1)) return false;
+  lu5_elim(L, 1, 2, 4);
+  // column 2: candidate row 3 (columns 2-4; row 2 is zero in column 4)
+  lu5_swap(L, 2, 3, 2, 5, 3);
+  if (!lu5_pivot(L, 2)) return false;
+  lu5_elim(L, 2, 3, 5);
+  // column 3: candidate row 4 (columns 3-4)
+  lu5_swap(L, 3, 4, 3, 5, 4);
+  if (!lu5_pivot(L, 3)) return false;
+  lu5_elim(L, 3, 4, 5);
+  return lu5_pivot(L, 4);
+}
+
+template <typename V>
+__device__ __forceinline__ void lu5_xchg(uint32_t sw, int bit, V &x, V &y) {
+  const bool ex = (sw >> bit) & 1u;
+  const V p = x, q = y;
+  x = ex ? q : p;
+  y = ex ? p : q;
 }
 
 template <typename W, typename V>
 __device__ __forceinline__ void lu5_solve(const LU5<W> &L, V b[5]) {
-  int s = 0;
-#pragma unroll
-  for (int col = 0; col < 5; ++col) {
-#pragma unroll
-    for (int r = col + 1; r < 5; ++r) {
-      const bool ex = (L.sw >> (s++)) & 1u;
-      const V x = b[col], y = b[r];
-      b[col] = ex ? y : x;
-      b[r] = ex ? x : y;
-    }
-#pragma unroll
-    for (int r = col + 1; r < 5; ++r) b[r] -= V(L.a[r][col]) * b[col];
-  }
-#pragma unroll
-  for (int r = 4; r >= 0; --r) {
-    V acc = b[r];
-#pragma unroll
-    for (int j = r + 1; j < 5; ++j) acc -= V(L.a[r][j]) * b[j];
-    b[r] = acc * V(L.inv[r]);
-  }
+  // forward: the exchanges and eliminations of the factor, column by column
+  lu5_xchg(L.sw, 0, b[0], b[1]);
+  lu5_xchg(L.sw, 1, b[0], b[2]);
+  b[1] -= V(L.a[1][0]) * b[0];
+  b[2] -= V(L.a[2][0]) * b[0];
+  lu5_xchg(L.sw, 2, b[1], b[2]);
+  b[2] -= V(L.a[2][1]) * b[1];
+  lu5_xchg(L.sw, 3, b[2], b[3]);
+  b[3] -= V(L.a[3][2]) * b[2];
+  lu5_xchg(L.sw, 4, b[3], b[4]);
+  b[4] -= V(L.a[4][3]) * b[3];
+  // back substitution over the non-zeros of U
+  b[4] = b[4] * V(L.inv[4]);
+  b[3] = (b[3] - V(L.a[3][4]) * b[4]) * V(L.inv[3]);
+  b[2] = (b[2] - V(L.a[2][3]) * b[3] - V(L.a[2][4]) * b[4]) * V(L.inv[2]);
+  b[1] = (b[1] - V(L.a[1][2]) * b[2] - V(L.a[1][3]) * b[3]) * V(L.inv[1]);
+  b[0] = (b[0] - V(L.a[0][1]) * b[1] - V(L.a[0][2]) * b[2] - V(L.a[0][3]) * b[3]) * V(L.inv[0]);
 }
 
 template <typename W> __device__ __forceinline__ W m_abs(W x) { return M<W>::abs(x); }
@@ -114,11 +144,11 @@ __device__ __forceinline__ W damp_factor(W Td, W E, W dTd, W dE) {
 // itself runs in W; the corrections are added to the FP64 state once at the
 // end.  Returns the iteration count, negative when nr_itr_limit was reached.
 // Inputs in W: T (= T_g, fixed), Tb / Eb (the starting point), g3 / g4 (the
-// starting point minus the substep's start) and dTg (T_d - T_g at the
-// starting point).  The FP64 path forms them exactly from the FP64 state; the
+// starting point minus the substep's start), dTg (T_d - T_g at the
+// starting point) and dtw (the substep).  The FP64 path forms them exactly from the FP64 state; the
 // mixed path from its W-precision view of the state and the LI increments.
 template <typename W>
-__device__ __forceinline__ int newton_dust_w(double u[5], W T, W Tb, W Eb, W g3, W g4, W dTg, double dt,
+__device__ __forceinline__ int newton_dust_w(double u[5], W T, W Tb, W Eb, W g3, W g4, W dTg, W dtw,
                                              const CellK<W> &c, const DevCfg &cfg, W tol) {
   typedef M<W> m;
   const bool frTd = cfg.flags & F_FTD, frE = cfg.flags & F_FE;
@@ -126,7 +156,7 @@ __device__ __forceinline__ int newton_dust_w(double u[5], W T, W Tb, W Eb, W g3,
   const uint32_t pm = cfg.pmask;
   const W G = c.Gpre * m::sqrt(T);
   const W gam = W(1) - W(0.8) * m::exp(W(-TLOW) * m::rcp(T));
-  const W rho = c.rho, fd = c.fd, dtw = W(dt);
+  const W rho = c.rho, fd = c.fd;
   W a3 = W(0), a4 = W(0);                       // accumulated corrections
   int result = -cfg.nr_itr_limit;
   bool polish = false;
@@ -167,8 +197,17 @@ __device__ __forceinline__ int newton_dust_w(double u[5], W T, W Tb, W Eb, W g3,
     if (polish) { result = it - 1; break; }
     if (lam == W(1) && m::abs(d0) <= tol * (Tb + a3) && m::abs(d1) <= tol * (Eb + a4)) polish = true;
   }
-  u[3] = fmax(u[3] + to_f64(a3), TCMB);
-  u[4] = fmax(u[4] + to_f64(a4), EFLOOR);
+  u[3] += to_f64(a3);
+  u[4] += to_f64(a4);
+  if constexpr (sizeof(W) == sizeof(double)) {
+    u[3] = fmax(u[3], TCMB);
+    u[4] = fmax(u[4], EFLOOR);
+  } else {
+    // the W iterate is already clamped: the FP64 floors can only act when
+    // it lies within W rounding of them
+    if (!(Tb + a3 > W(TCMB * 1.001))) u[3] = fmax(u[3], TCMB);
+    if (!(Eb + a4 > W(EFLOOR * 1.001))) u[4] = fmax(u[4], EFLOOR);
+  }
   return result;
 }
 
@@ -245,14 +284,33 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
   const double rem = dt_h - c.t;
   // c.nri > 0: the update of this substep was rejected c.nri times (below)
   // and is redone with the step halved as often (exact powers of two)
-  const bool fits = (dtc >= rem) || (rem - dtc <= 1e-12 * dt_h);
+  bool fits;
+  double dts;
+  W dw;
+  if constexpr (MIXED) {
+    // W-precision control (the FP64 pipe is the scarce one): the substep
+    // takes the time left once dt_c reaches it to W rounding.  dt_c is
+    // finite when it falls short of the time left, so only its sign and
+    // NaN need a test.
+    const W remw = to_w<W>(rem);
+    fits = dtcw >= remw;
+    if (!(fits || dtcw > W(0))) { c.st |= ST_BADSTEP; return true; }
+    dts = fits ? rem : dtc;
+    dw = fits ? remw : dtcw;
+    if (c.nri != 0) {
+      dts *= pow2_neg<double>(c.nri);
+      dw *= pow2_neg<W>(c.nri);
+    }
+  } else {
+    fits = (dtc >= rem) || (rem - dtc <= 1e-12 * dt_h);
+    dts = (fits ? rem : dtc) * pow2_neg<double>(c.nri);
+    if (!(dts > 0.0) || !isfinite(dts)) { c.st |= ST_BADSTEP; return true; }
+    dw = (fits ? to_w<W>(rem) : dtcw) * pow2_neg<W>(c.nri);
+  }
   const bool last = fits && c.nri == 0;
-  const double dts = (fits ? rem : dtc) * pow2_neg<double>(c.nri);
-  if (!(dts > 0.0) || !isfinite(dts)) { c.st |= ST_BADSTEP; return true; }
   // A = I - dt J, b = dt F (scaled rows and columns)
   LU5<W> L;
   W x[5];
-  const W dw = (fits ? to_w<W>(rem) : dtcw) * pow2_neg<W>(c.nri);
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
 #pragma unroll
@@ -354,7 +412,7 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
         d4 = to_w<W>(c.u[4] - u0[4]);
       }
       const W d2 = S.uf[2] * x[2];
-      it = newton_dust_w<W>(c.u, S.uf[2] + d2, S.uf[3] + d3, S.uf[4] + d4, d3, d4, S.dTdg + (d3 - d2), dts, c.k,
+      it = newton_dust_w<W>(c.u, S.uf[2] + d2, S.uf[3] + d3, S.uf[4] + d4, d3, d4, S.dTdg + (d3 - d2), dw, c.k,
                             cfg, cw.nr_tol);
     } else {
       const double lam = damp_factor<double>(u0[3], u0[4], c.u[3] - u0[3], c.u[4] - u0[4]);
