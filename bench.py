@@ -39,12 +39,12 @@ YR = inputs.YR
 # divided by the substeps of that launch (GRF 128^3 workload, dt = 1e3 yr,
 # C_d = 1e4); profiles/sfchem_li_{mixed,fp64}_grf128.md.
 WORK_PER_SUBSTEP = {
-    "mixed": {"fp32_flops": 1504.9, "fp64_flops": 59.4},
-    "fp64": {"fp32_flops": 7.5, "fp64_flops": 2060.8},
+    "mixed": {"fp32_flops": 1461.7, "fp64_flops": 54.4},
+    "fp64": {"fp32_flops": 7.5, "fp64_flops": 2004.8},
 }
-# DRAM bytes per cell of one solver launch (same captures: 249.1 MB for
-# 2,097,152 cells, mixed; 274.9 MB, FP64).
-DRAM_BYTES_PER_CELL = {"mixed": 249.05e6 / 2097152, "fp64": 274.93e6 / 2097152}
+# DRAM bytes per cell of one solver launch (same captures: 252.6 MB for
+# 2,097,152 cells, mixed; 274.8 MB, FP64).
+DRAM_BYTES_PER_CELL = {"mixed": 252.55e6 / 2097152, "fp64": 274.77e6 / 2097152}
 # GB300 ALU peaks from unit counts and the SM clock: 152 SMs; FP32 128
 # lanes/SM (256 flops/clk); FP64 2 DFMA/clk/SM (4 flops/clk) -- the
 # "peak_sustained" of the FP64 pipe that ncu reports, 1.26 TFLOP/s at 2.07 GHz.
@@ -59,12 +59,16 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    p.add_argument("--workload", default="gmc256", choices=("gmc256", "grf128", "amr3000", "uniform4096"))
+    p.add_argument("--workload", default="gmc256", choices=("gmc256", "grf128", "amr3000", "uniform4096", "be"))
+    p.add_argument("--Z", type=float, default=1.0, choices=(1.0, 1e-2, 1e-4),
+                   help="metallicity of the Bonnor-Ebert sphere workload (Z / Z_sun)")
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-ff", action="store_true", help="skip the mixed leg with the FP32 error-free refinement")
     p.add_argument("--no-nr", action="store_true", help="skip the Newton-Raphson reference leg")
     p.add_argument("--sweep", action="store_true", help="run the dt x C_d sweep on the GRF 128^3 grid instead")
     p.add_argument("--sweep-precision", default="fp64", choices=("fp64", "mixed"))
+    p.add_argument("--sweep-z", action="store_true",
+                   help="run the metallicity / C_d sweep on the Bonnor-Ebert sphere instead")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (error check, cpu_baseline)")
     p.add_argument("--sample", type=int, default=4096, help="cells checked against the oracle")
@@ -73,8 +77,15 @@ def parse():
 
 
 # ------------------------------------------------------------------ workloads
-def make_workload(name: str, rank: int = 0):
+def make_workload(name: str, rank: int = 0, Z: float = 1.0):
     """(cells, block_offset, block_dt, cd_factor, description)"""
+    if name == "be":
+        cells, off, lvl = inputs.cells_be(Z)
+        bdt = np.full(len(off) - 1, inputs.be_dt())
+        return cells, off, bdt, 1e3, dict(
+            workload="initial Bonnor-Ebert sphere, nested grids l_max = 2 (1408 blocks of 8^3)",
+            cells=len(cells["n_H"]), Z=Z, dt_yr=inputs.be_dt() / YR, cd_factor=1e3, C_d=1e7,
+            blocks=len(bdt), block_cells=512)
     if name == "gmc256":
         cells = inputs.cells_gmc(256, seed=1005 + rank)
         cells, off = inputs.block_major(cells, 256, 16)
@@ -186,7 +197,8 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    cells, off, bdt, cd, desc = make_workload(args.workload, rank)
+    cells, off, bdt, cd, desc = make_workload(args.workload, rank, args.Z)
+    Z = desc.get("Z", 1.0)
     n = len(cells["n_H"])
     stream = torch.cuda.current_stream()
 
@@ -223,7 +235,7 @@ def run_ours(args, rank, world, local_rank):
 
     res = {}
     # ---- mixed precision, batched (the headline)
-    sm = sf.Solver("mixed")
+    sm = sf.Solver("mixed", Z=Z)
     if not args.no_autotune:
         reset()
         sm.autotune(d, off, bdt, cd)
@@ -236,7 +248,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- mixed precision with the error-free FP32 refinement residual
     out_ff = None
     if not args.no_ff:
-        sff = sf.Solver("mixed", flags=sf.F_REFINE_FF)
+        sff = sf.Solver("mixed", flags=sf.F_REFINE_FF, Z=Z)
         sff.set_launch(**sm.get_launch())
         ms_ff, wall_ff, st_ff = timed_leg(sff, args.steps, args.warmup)
         out_ff = sf.to_host({k: d[k] for k in sf.STATE_FIELDS + ("status", "n_sub")})
@@ -245,7 +257,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- plain FP64, batched, same workload
     out_d = None
     if not args.no_fp64:
-        sd = sf.Solver("fp64")
+        sd = sf.Solver("fp64", Z=Z)
         sd.set_launch(64, 0, 32)           # the fastest of the shapes timed on the GRF 128^3 workload
         k64 = max(1, min(args.steps, 2))   # the slow leg: 1 warm-up, 2 timed steps
         ms_d, wall_d, st_d = timed_leg(sd, k64, 1)
@@ -254,7 +266,7 @@ def run_ours(args, rank, world, local_rank):
         sd.close()
     # ---- the Newton-Raphson reference solver (Sec. 2.2.8) on the same workload
     if not args.no_nr and np.all(bdt == bdt[0]):
-        snr = sf.Solver("fp64", n_sub_max=2000)
+        snr = sf.Solver("fp64", n_sub_max=2000, Z=Z)
         for _ in range(1):
             reset()
             snr.step_nr(d, float(bdt[0]), cd)
@@ -344,8 +356,8 @@ def run_ours(args, rank, world, local_rank):
     if "fp64" in res:
         line["roofline_fp64"] = roofline(res, clk, n, "fp64")
     if rank == 0 and not args.no_cpu:
-        line["error_vs_oracle"] = error_vs_oracle(cells, off, bdt, cd, out_m, out_d, args.sample, out_ff)
-        line["cpu_baseline"] = cpu_baseline(cells, off, bdt, cd, args.cpu_seconds)
+        line["error_vs_oracle"] = error_vs_oracle(cells, off, bdt, cd, out_m, out_d, args.sample, out_ff, Z=Z)
+        line["cpu_baseline"] = cpu_baseline(cells, off, bdt, cd, args.cpu_seconds, Z=Z)
     return line
 
 
@@ -378,14 +390,21 @@ def roofline(res, clk, n_cells, leg="mixed"):
     return out
 
 
-def error_vs_oracle(cells, off, bdt, cd, out_m, out_d, sample, out_ff=None):
+def oracle_config(Z: float = 1.0):
+    import oracle
+    c = oracle.default_config()
+    c.Z = Z
+    return c
+
+
+def error_vs_oracle(cells, off, bdt, cd, out_m, out_d, sample, out_ff=None, Z=1.0):
     """Mixed and FP64 results against the oracle on a seeded sample of cells."""
     import oracle
     n = len(cells["n_H"])
     idx = np.sort(np.random.default_rng(123).choice(n, min(sample, n), replace=False))
     blk = np.searchsorted(off, idx, side="right") - 1
     sub = inputs.subset(cells, idx)
-    ref = oracle.li_step(sub, bdt[blk], cd)
+    ref = oracle.li_step(sub, bdt[blk], cd, oracle_config(Z))
     out = {"sample_cells": int(idx.size)}
     for name, got in (("mixed", out_m), ("mixed_ff", out_ff), ("fp64", out_d)):
         if got is None:
@@ -402,7 +421,7 @@ def error_vs_oracle(cells, off, bdt, cd, out_m, out_d, sample, out_ff=None):
     return out
 
 
-def cpu_baseline(cells, off, bdt, cd, target_s):
+def cpu_baseline(cells, off, bdt, cd, target_s, Z=1.0):
     """The oracle on the host cores, on a bounded sample of the workload."""
     import oracle
     n = len(cells["n_H"])
@@ -413,7 +432,7 @@ def cpu_baseline(cells, off, bdt, cd, target_s):
         blk = np.searchsorted(off, idx, side="right") - 1
         sub = inputs.subset(cells, idx)
         t0 = time.perf_counter()
-        oracle.li_step(sub, bdt[blk], cd)
+        oracle.li_step(sub, bdt[blk], cd, oracle_config(Z))
         dt = time.perf_counter() - t0
         if dt >= 0.5 * target_s or m >= n or m >= (1 << 22):
             break
@@ -428,13 +447,14 @@ def run_reference(args):
     """The oracle (plain FP64 CPU LI step) timed on the host cores, each step
     one bounded sample of the same workload."""
     import oracle
-    cells, off, bdt, cd, desc = make_workload(args.workload, 0)
+    cells, off, bdt, cd, desc = make_workload(args.workload, 0, args.Z)
+    ocfg = oracle_config(desc.get("Z", 1.0))
     n = len(cells["n_H"])
     rng = np.random.default_rng(99)
     # size the per-step sample so the whole run stays within a few minutes
     probe = np.sort(rng.choice(n, min(2048, n), replace=False))
     t0 = time.perf_counter()
-    oracle.li_step(inputs.subset(cells, probe), bdt[np.searchsorted(off, probe, side="right") - 1], cd)
+    oracle.li_step(inputs.subset(cells, probe), bdt[np.searchsorted(off, probe, side="right") - 1], cd, ocfg)
     per_cell = (time.perf_counter() - t0) / probe.size
     budget = 120.0 / max(args.steps + args.warmup, 1)
     m = int(min(n, max(1024, budget / max(per_cell, 1e-9))))
@@ -444,7 +464,7 @@ def run_reference(args):
         sub = inputs.subset(cells, idx)
         blk = np.searchsorted(off, idx, side="right") - 1
         t0 = time.perf_counter()
-        oracle.li_step(sub, bdt[blk], cd)
+        oracle.li_step(sub, bdt[blk], cd, ocfg)
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     sec = float(np.mean(times))
@@ -531,7 +551,8 @@ def run_sweep(args):
             for k in ("T_g", "T_d", "y_H2", "y_e"):
                 floor = 1e-6 if k.startswith("y_") else 1e-300
                 e = np.abs(out[k] - base[k]) / np.maximum(np.abs(base[k]), floor)
-                dev[k] = {"max": float(e.max()), "median": float(np.median(e))}
+                dev[k] = {"max": float(e.max()), "p99": float(np.percentile(e, 99)),
+                          "median": float(np.median(e)), "frac_above_1e-3": float((e > 1e-3).mean())}
             ns = out["n_sub"]
             rows.append({"dt_yr": dt_yr, "cd_factor": cd, "C_d": cd * 1e4, "ms": ms,
                          "cell_updates_per_s": n / (ms * 1e-3),
@@ -544,12 +565,73 @@ def run_sweep(args):
             "rows": rows}
 
 
+def run_sweep_z(args):
+    """Metallicity and C_d sweep on the initial Bonnor-Ebert sphere (Sec. 4.3,
+    the settings of its solver-performance comparison): the LI method (mixed
+    batched, plain FP64 batched) and the Newton-Raphson reference on the same
+    GPU; cell-updates/s, substeps per cell and the LI - NR difference."""
+    import torch
+    import paper_2604_21438_gb300 as sf
+    rows = []
+    for Z, cds in ((1.0, (1.0, 10.0, 100.0, 1e3, 1e4)), (1e-2, (1e3,)), (1e-4, (1e3,))):
+        cells, off, _ = inputs.cells_be(Z)
+        dt = inputs.be_dt()
+        bdt = np.full(len(off) - 1, dt)
+        n = len(cells["n_H"])
+        d = sf.to_device(cells)
+        pristine = {k: d[k].clone() for k in sf.STATE_FIELDS}
+        for cd in cds:
+            row = {"Z": Z, "C_d": cd * 1e4, "cells": n, "dt_yr": dt / YR}
+            outs = {}
+            for leg in ("mixed", "fp64", "nr"):
+                kw = {"n_sub_max": 2000} if leg == "nr" else {}
+                s = sf.Solver("mixed" if leg == "mixed" else "fp64", Z=Z, **kw)
+                times = []
+                for rep in range(4):
+                    for k in sf.STATE_FIELDS:
+                        d[k].copy_(pristine[k])
+                    if rep == 1:
+                        s.stats_reset()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    if leg == "nr":
+                        s.step_nr(d, dt, cd)
+                    else:
+                        s.step_batched(d, off, bdt, cd)
+                    b.record()
+                    torch.cuda.synchronize()
+                    if rep >= 1:
+                        times.append(a.elapsed_time(b))
+                st = s.stats()
+                s.close()
+                outs[leg] = sf.to_host({k: d[k] for k in sf.STATE_FIELDS + ("n_sub", "status")})
+                ms = float(np.mean(times))
+                row[leg] = {"cell_updates_per_s": n / (ms * 1e-3), "ms": ms,
+                            "n_sub_av": st["substeps"] / max(st["cells"], 1),
+                            "tight_fraction": st["tight_cells"] / max(st["cells"], 1),
+                            "noconv_cells": st["noconv_cells"]}
+            for name, a in (("li_vs_nr", outs["fp64"]), ("mixed_vs_fp64", outs["mixed"])):
+                b = outs["nr"] if name == "li_vs_nr" else outs["fp64"]
+                row[name] = {}
+                for k in ("T_g", "T_d"):
+                    e = np.abs(a[k] - b[k]) / np.abs(b[k])
+                    row[name][k] = {"max": float(e.max()), "p99": float(np.percentile(e, 99)),
+                                    "median": float(np.median(e))}
+            rows.append(row)
+        del d, pristine
+    return {"sweep": "Z x C_d on the initial Bonnor-Ebert sphere", "rows": rows}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.sweep:
         if rank == 0:
             print(json.dumps(run_sweep(args)))
+        return
+    if args.sweep_z:
+        if rank == 0:
+            print(json.dumps(run_sweep_z(args)))
         return
     if args.impl == "reference":
         if rank == 0:

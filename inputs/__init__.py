@@ -27,6 +27,19 @@ which are full simulations this library does not reproduce):
   anti-correlated with it and clamped to 10..1e4 K, 8 seeded point sources
   whose EUV/FUV fields fall as 1/r^2 and are shielded by a local column
   n_H min(r, 8 dx); dt = 1e3 yr, dust-capacity factor 100.
+* ``cells_be``       -- the initial Bonnor-Ebert sphere of the collapse tests
+  (Sec. 4.3): a critical isothermal sphere (dimensionless radius 6.45, the
+  Lane-Emden profile integrated here), density raised by 1.2, central
+  n_H = 1.2e4 cm^-3, the edge density outside; nested grids with l_max = 2,
+  each level 8^3 blocks of 8^3 cells, the level-0 box spanning the sphere's
+  diameter and each finer level the inner half of the one above (1408 leaf
+  blocks, 720,896 cells); T_g and abundances are the paper's one-zone values
+  for the metallicity (Table BEsphere: y_H2 and y_H+ as printed, y_e = y_H+,
+  y_H from H-nuclei conservation, which matches the printed y_H to its
+  rounding), T_d = T_g, no UV (G0 = n_EUV = 0: the test evolves IR radiation
+  only), E_IR = (c / c~) a T_d^4, N_H2 = y_H2 n_H r; synchronous dt = half the
+  finest level's sound-crossing time of a cell (5.2e3 yr, the same for every
+  metallicity because the sphere scales with the sound speed).
 """
 from __future__ import annotations
 
@@ -212,6 +225,83 @@ def cells_gmc(n: int = 256, seed: int = 1005, box_pc: float = 3.0) -> dict:
     c["N_H2"] = c["y_H2"] * nH * 8.0 * dx
     c["E_IR"] = _e_ir(c["T_d"])
     return _finish(c)
+
+
+# Table BEsphere: initial T_g [K], y_H2 and y_H+ of the Bonnor-Ebert spheres
+# by metallicity Z / Z_sun (Sec. 4.3).
+BE_SEEDS = {1.0: (5.0, 4.98e-1, 1.27e-7), 1e-2: (21.0, 3.47e-2, 1.99e-7), 1e-4: (190.0, 1.18e-3, 8.29e-7)}
+
+
+def _lane_emden(xi_max: float = 6.45, h: float = 1e-3):
+    """Isothermal Lane-Emden solution psi(xi) (rho = rho_c exp(-psi)), RK4."""
+    def f(x, y):
+        psi, dpsi = y
+        return np.array([dpsi, np.exp(-psi) - 2.0 * dpsi / x])
+    x = 1e-4
+    y = np.array([x * x / 6.0, x / 3.0])     # series start
+    xs, ps = [0.0, x], [0.0, y[0]]
+    while x < xi_max:
+        k1 = f(x, y)
+        k2 = f(x + h / 2, y + h / 2 * k1)
+        k3 = f(x + h / 2, y + h / 2 * k2)
+        k4 = f(x + h, y + h * k3)
+        y = y + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        x += h
+        xs.append(x)
+        ps.append(y[0])
+    return np.array(xs), np.array(ps)
+
+
+def cells_be(Z: float = 1.0, levels: int = 3):
+    """Initial Bonnor-Ebert sphere on nested grids (see the module docstring).
+    Returns (cells, block_offset, block_level), blocks of 8^3 cells stored
+    contiguously (x fastest inside a block)."""
+    T0, y2, yp = BE_SEEDS[Z]
+    b = np.arange(8)
+    bz, by, bx = (a.reshape(-1) for a in np.meshgrid(b, b, b, indexing="ij"))
+    inner = (bz >= 2) & (bz <= 5) & (by >= 2) & (by <= 5) & (bx >= 2) & (bx <= 5)
+    c8 = np.arange(8)
+    cz, cy, cx = (a.reshape(-1) for a in np.meshgrid(c8, c8, c8, indexing="ij"))
+    xi_max = 6.45
+    xs, ps = _lane_emden(xi_max)
+    r_list, lev = [], []
+    for l in range(levels):
+        keep = np.ones(512, bool) if l == levels - 1 else ~inner
+        h = xi_max / 32.0 / 2.0 ** l       # cell size in units of the BE length
+        for k in np.nonzero(keep)[0]:
+            x = (bx[k] * 8 + cx - 32 + 0.5) * h
+            y = (by[k] * 8 + cy - 32 + 0.5) * h
+            z = (bz[k] * 8 + cz - 32 + 0.5) * h
+            r_list.append(np.sqrt(x * x + y * y + z * z))
+            lev.append(l)
+    xi = np.concatenate(r_list)
+    psi = np.interp(np.minimum(xi, xi_max), xs, ps)
+    nH = 1.2e4 * np.exp(-psi)
+    # BE length c_s / sqrt(4 pi G rho_c) in cm (isothermal c_s, mu = 2.3)
+    kB, mH, G = 1.380649e-16, 1.6726e-24, 6.674e-8
+    cs = np.sqrt(kB * T0 / (2.3 * mH))
+    Lbe = cs / np.sqrt(4.0 * np.pi * G * 1.4 * mH * 1.2e4)
+    n = len(xi)
+    c = {}
+    c["n_H"] = nH
+    c["T_g"] = np.full(n, T0)
+    c["T_d"] = np.full(n, T0)
+    c["y_e"] = np.full(n, yp)
+    c["y_H2"] = np.full(n, y2)
+    c["G0"] = np.zeros(n)
+    c["n_EUV"] = np.zeros(n)
+    c["N_H2"] = y2 * nH * np.maximum(xi, 0.5 * xi_max / 32.0 / 2.0 ** (levels - 1)) * Lbe
+    c["E_IR"] = _e_ir(c["T_d"])
+    block_offset = np.arange(len(lev) + 1, dtype=np.int64) * 512
+    return _finish(c), block_offset, np.asarray(lev, dtype=np.int32)
+
+
+def be_dt(levels: int = 3) -> float:
+    """Synchronous step of the sphere: half the finest cell's sound-crossing
+    time (independent of T_g, see the module docstring)."""
+    kB, mH, G = 1.380649e-16, 1.6726e-24, 6.674e-8
+    # dx_f / c_s = (6.45 / 32 / 2^(levels-1)) / sqrt(4 pi G rho_c)
+    return 0.5 * (6.45 / 32.0 / 2.0 ** (levels - 1)) / np.sqrt(4.0 * np.pi * G * 1.4 * mH * 1.2e4)
 
 
 def paper_case(case: int) -> dict:

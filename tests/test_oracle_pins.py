@@ -250,14 +250,19 @@ def test_conservation_and_bounds():
     assert np.all(o["T_g"] >= 2.725) and np.all(o["T_d"] >= 2.725)
 
 
-def test_energy_invariant_of_appendix_c():
+@pytest.mark.parametrize("Z", [1.0, 1e-2, 1e-4])
+def test_energy_invariant_of_appendix_c(Z):
     """P7: with the gas heating/cooling of Table 4 switched off, the LI rows of
-    Appendix C conserve rho C_d dT_d + dE_IR + rho alpha_g dT_g = rho dt E_UV
-    in every substep (their column sums cancel)."""
+    Appendix C conserve rho f_d C_d dT_d + dE_IR + rho alpha_g dT_g =
+    rho f_d dt E_UV in every substep (their column sums cancel once the dust
+    row, which is written per unit of solar-metallicity dust, is weighted by
+    the dust abundance f_d = Z / Z_sun; Eqs. ap_eq:Td2, ap_eq:Tg_2 and the IR
+    row).  A misplaced or missing f_d breaks it at Z != Z_sun."""
     cell = one_cell(n_H=1e4, T_g=40.0, T_d=15.0, G0=100.0, E_IR=1e-6)
     cfg = oracle.default_config(reaction_mask=0,
                                 process_mask=oracle.P_GASGRAIN | oracle.P_DUST_UV | oracle.P_DUST_EMIT
                                 | oracle.P_DUST_IRABS)
+    cfg.Z = Z
     cd = 1000.0
     dt = 1e6
     rec, st = oracle.li_trace(cell, dt, cd, cfg)
@@ -265,12 +270,18 @@ def test_energy_invariant_of_appendix_c():
     u0 = np.array([cell[k] for k in ("y_H2", "y_e", "T_g", "T_d", "E_IR")])
     _, _, _, M, _, aux = oracle.system(cell["n_H"], u0, cell["G0"], 0.0, cell["N_H2"], 1.0, cd, cfg)
     rho, alpha_g, EUV = aux[0], aux[1], aux[2]
+    wd = rho * Z * cd * 1e4
     prev = u0
     for t_end, dts, *u in rec:
         u = np.array(u)
-        lhs = rho * cd * 1e4 * (u[3] - prev[3]) + (u[4] - prev[4]) + rho * alpha_g * (u[2] - prev[2])
-        scale = rho * cd * 1e4 * abs(u[3] - prev[3]) + abs(u[4] - prev[4]) + rho * alpha_g * abs(u[2] - prev[2])
-        assert abs(lhs - rho * dts * EUV) <= 1e-9 * max(scale, rho * dts * EUV)
+        lhs = wd * (u[3] - prev[3]) + (u[4] - prev[4]) + rho * alpha_g * (u[2] - prev[2])
+        scale = wd * abs(u[3] - prev[3]) + abs(u[4] - prev[4]) + rho * alpha_g * abs(u[2] - prev[2])
+        src = rho * Z * dts * EUV
+        # plus the rounding of the recorded states the differences are taken
+        # from (E_IR changes by ~1e-11 of itself per substep here)
+        ulp = 4 * np.finfo(float).eps * (wd * (abs(u[3]) + abs(prev[3])) + abs(u[4]) + abs(prev[4]) +
+                                         rho * alpha_g * (abs(u[2]) + abs(prev[2])))
+        assert abs(lhs - src) <= 1e-9 * max(scale, src) + ulp
         prev = u
 
 
