@@ -7,7 +7,8 @@ CPU fallback: importing the binding on a machine without the library raises.
 
 Low level: the ctypes structures and functions carry the C names of
 ``include/sfchem.h`` (``sfchem_init``, ``sfchem_step``, ...).  High level:
-``Solver`` wraps a context and takes dicts of CUDA float64 tensors.
+``Solver`` wraps a context and takes dicts of CUDA float64 tensors
+(``Solver.step_host``: CPU tensors).
 """
 from __future__ import annotations
 
@@ -77,7 +78,8 @@ _lib = None
 EXPORTS = ("sfchem_config_default", "sfchem_config_validate", "sfchem_init", "sfchem_set_config",
            "sfchem_step", "sfchem_step_nr", "sfchem_step_batched", "sfchem_set_launch", "sfchem_get_launch",
            "sfchem_autotune", "sfchem_stats", "sfchem_stats_reset", "sfchem_finalize",
-           "sfchem_strerror", "sfchem_last_cuda_error", "sfchem_version", "sfchem_step_batched_noalloc")
+           "sfchem_strerror", "sfchem_last_cuda_error", "sfchem_version", "sfchem_step_batched_noalloc",
+           "sfchem_step_host")
 # scratch limits of sfchem_step_batched_noalloc (include/sfchem.h)
 NOALLOC_MAX_BLOCKS, NOALLOC_MAX_CHUNKS = 4096, 65536
 
@@ -116,6 +118,8 @@ def lib():
                                   P(ctypes.c_double), i32, dbl, vp]
     L.sfchem_step_batched_noalloc.argtypes = [P(sfchem_config_t), P(sfchem_state_t), P(sfchem_fields_t),
                                               P(ctypes.c_int64), P(ctypes.c_double), i32, dbl, vp]
+    L.sfchem_step_host.argtypes = [vp, P(sfchem_state_t), P(sfchem_fields_t), P(ctypes.c_int64),
+                                   P(ctypes.c_double), i32, dbl, i64, vp]
     L.sfchem_stats.argtypes = [vp, P(sfchem_stats_t)]
     L.sfchem_stats_reset.argtypes = [vp]
     L.sfchem_finalize.argtypes = [vp]
@@ -152,26 +156,27 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
-def _check_tensor(name, t, n, dtype):
+def _check_tensor(name, t, n, dtype, cuda=True):
     import torch
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError(f"{name} must be a CUDA tensor")
+    if not isinstance(t, torch.Tensor) or t.is_cuda != cuda:
+        raise TypeError(f"{name} must be a {'CUDA' if cuda else 'CPU'} tensor")
     if t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
         raise ValueError(f"{name} must be a contiguous {dtype} tensor of {n} elements")
 
 
-def make_structs(cells: dict, n: int):
-    """Build (sfchem_state_t, sfchem_fields_t) from a dict of CUDA tensors."""
+def make_structs(cells: dict, n: int, cuda: bool = True):
+    """Build (sfchem_state_t, sfchem_fields_t) from a dict of CUDA tensors
+    (cuda=False: CPU tensors, for sfchem_step_host)."""
     import torch
     for k in STATE_FIELDS + INPUT_FIELDS:
-        _check_tensor(k, cells[k], n, torch.float64)
+        _check_tensor(k, cells[k], n, torch.float64, cuda)
     for k in ("y_H", "y_Hp", "y_Hm"):
         if cells.get(k) is not None:
-            _check_tensor(k, cells[k], n, torch.float64)
+            _check_tensor(k, cells[k], n, torch.float64, cuda)
     if cells.get("status") is not None:
-        _check_tensor("status", cells["status"], n, torch.uint8)
+        _check_tensor("status", cells["status"], n, torch.uint8, cuda)
     if cells.get("n_sub") is not None:
-        _check_tensor("n_sub", cells["n_sub"], n, torch.int32)
+        _check_tensor("n_sub", cells["n_sub"], n, torch.int32, cuda)
     st = sfchem_state_t(
         _ptr(cells["n_H"]), _ptr(cells["T_g"]), _ptr(cells["T_d"]), _ptr(cells["E_IR"]),
         _ptr(cells["y_H2"]), _ptr(cells["y_e"]), _ptr(cells.get("y_H")), _ptr(cells.get("y_Hp")),
@@ -240,6 +245,24 @@ class Solver:
             off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
             bdt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nb, float(cd_factor),
             _stream_handle(stream)), "sfchem_step_batched")
+
+    def step_host(self, cells: dict, block_offset, block_dt, cd_factor: float = 1.0, slice_cells: int = 0,
+                  stream=None):
+        """sfchem_step_host: `cells` holds CPU tensors (pinned for overlapped
+        copies); returns when the results are in them."""
+        import numpy as np
+        n = cells["n_H"].numel()
+        st, fl = make_structs(cells, n, cuda=False)
+        off = np.ascontiguousarray(block_offset, dtype=np.int64)
+        bdt = np.ascontiguousarray(block_dt, dtype=np.float64)
+        nb = len(bdt)
+        if len(off) != nb + 1 or off[-1] != n:
+            raise ValueError("block_offset must have n_blocks + 1 entries ending at n_cells")
+        _check(lib().sfchem_step_host(
+            self.handle, ctypes.byref(st), ctypes.byref(fl),
+            off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            bdt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nb, float(cd_factor), int(slice_cells),
+            _stream_handle(stream)), "sfchem_step_host")
 
     def autotune(self, cells: dict, block_offset, block_dt, cd_factor: float = 1.0, stream=None):
         import numpy as np

@@ -39,7 +39,9 @@ def _sources():
 
 
 def stale() -> bool:
-    for lib, srcs in ((LIB, _sources()), (BENCH_LIB, [os.path.join(CSRC, u) for u in BENCH_UNITS])):
+    # the benchmark library also includes the solver's device header
+    bench_srcs = [os.path.join(CSRC, u) for u in BENCH_UNITS] + [os.path.join(CSRC, "li_device.cuh")]
+    for lib, srcs in ((LIB, _sources()), (BENCH_LIB, bench_srcs)):
         if not os.path.exists(lib):
             return True
         t = os.path.getmtime(lib)

@@ -82,12 +82,58 @@ template <> struct M<double> {
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
   static __device__ __forceinline__ double abs(double x) { return ::fabs(x); }
 };
+// FP32 (mixed path): the hardware approximations of the PTX ISA (ex2, lg2,
+// rcp, sqrt .approx.ftz) with the corrections below, instead of the IEEE
+// division and the full-range libm sequences, whose code more than tripled
+// the kernel's size and left a third of its instruction fetches missing the
+// instruction cache.  Accuracy, checked against CUDA's expf, logf, 1/x and
+// sqrtf by tests/test_gpu_math.py: exp within 4 ulp on [-87, 88]; log within
+// 4 ulp for x >= 2.7 (it is only taken of temperatures >= T_CMB, where
+// ln x >= 1 and the absolute error bound of lg2.approx is also a relative
+// one); rcp and sqrt within 1 ulp.  Results below the FP32 normal range
+// flush to zero.
+__device__ __forceinline__ float ptx_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ptx_lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ptx_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ptx_sqrt(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 template <> struct M<float> {
-  static __device__ __forceinline__ float exp(float x) { return ::expf(x); }
-  static __device__ __forceinline__ float log(float x) { return ::logf(x); }
+  // exp(x) = 2^h 2^e with h = fl(x log2 e) and e its error: the rounding
+  // error of the product, exact by one FMA (the FMA form of Dekker's exact
+  // product), plus x times the part of log2 e that a float drops.  2^e is
+  // taken to first order (|e| < 2^-17); e is clamped so that x = -inf gives
+  // 0, and an overflowed 2^h is returned as it is.
+  static __device__ __forceinline__ float exp(float x) {
+    const float L2E = 1.44269502f, L2E_TAIL = 1.92596299e-8f;   // log2 e = L2E + L2E_TAIL
+    const float h = x * L2E;
+    const float e = fmaf(x, L2E, -h) + x * L2E_TAIL;
+    const float p = ptx_ex2(h);
+    const float q = fmaf(p, fminf(fmaxf(e, -1.0f), 1.0f) * 0.693147181f, p);
+    return p < __int_as_float(0x7f800000) ? q : p;
+  }
+  static __device__ __forceinline__ float log(float x) { return ptx_lg2(x) * 0.693147181f; }
   static __device__ __forceinline__ float log1p(float x) { return ::log1pf(x); }
-  static __device__ __forceinline__ float sqrt(float x) { return ::sqrtf(x); }
-  static __device__ __forceinline__ float rcp(float x) { return 1.0f / x; }
+  static __device__ __forceinline__ float sqrt(float x) { return ptx_sqrt(x); }
+  // one Newton-Raphson step r' = r + r (1 - x r) on the hardware estimate
+  static __device__ __forceinline__ float rcp(float x) {
+    const float r = ptx_rcp(x);
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+  }
   static __device__ __forceinline__ float abs(float x) { return ::fabsf(x); }
 };
 

@@ -46,7 +46,7 @@ template <typename W>
 __device__ __forceinline__ bool lu5_pivot(LU5<W> &L, int p) {
   const W piv = L.a[p][p];
   if (!(M<W>::abs(piv) > W(0))) return false;
-  L.inv[p] = W(1) / piv;
+  L.inv[p] = M<W>::rcp(piv);
   return true;
 }
 

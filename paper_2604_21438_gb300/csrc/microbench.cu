@@ -1,9 +1,11 @@
 // microbench.cu -- FMA-throughput microbenchmarks used as measured ALU
-// denominators of the roofline (FP64 and FP32 vector pipes).  Each thread
-// runs 8 independent FMA chains in registers; one launch covers every SM
-// several times over.  Not part of the solver.
+// denominators of the roofline (FP64 and FP32 vector pipes), and a device
+// check of the solver's FP32 math functions against CUDA's.  Each FMA thread
+// runs 8 independent chains in registers; one launch covers every SM several
+// times over.  Not part of the solver.
 #include <cuda_runtime.h>
 #include <cstdint>
+#include "li_device.cuh"
 
 template <typename T>
 __global__ void __launch_bounds__(256) fma_chain(T *out, int iters, T a, T b) {
@@ -53,4 +55,36 @@ extern "C" int sfbench_fma_fp64(int iters, double *flops_per_s, float *ms) {
 }
 extern "C" int sfbench_fma_fp32(int iters, double *flops_per_s, float *ms) {
   return run<float>(iters, 8, flops_per_s, ms);
+}
+
+// fn: 0 exp, 1 log, 2 rcp, 3 sqrt.  ours[i] = the solver's M<float> function
+// of x[i], ref[i] = CUDA's expf / logf / 1.0f / x / sqrtf.  Host buffers.
+__global__ void math_check(int fn, int n, const float *x, float *ours, float *ref) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = x[i];
+  typedef sfc::M<float> m;
+  float a = 0.f, b = 0.f;
+  if (fn == 0) { a = m::exp(v); b = expf(v); }
+  else if (fn == 1) { a = m::log(v); b = logf(v); }
+  else if (fn == 2) { a = m::rcp(v); b = 1.0f / v; }
+  else { a = m::sqrt(v); b = sqrtf(v); }
+  ours[i] = a;
+  ref[i] = b;
+}
+
+extern "C" int sfbench_math_check(int fn, int n, const float *x, float *ours, float *ref) {
+  if (n <= 0 || fn < 0 || fn > 3 || !x || !ours || !ref) return 1;
+  float *d = nullptr;
+  if (cudaMalloc(&d, sizeof(float) * 3 * (size_t)n) != cudaSuccess) return 1;
+  int rc = 0;
+  if (cudaMemcpy(d, x, sizeof(float) * n, cudaMemcpyHostToDevice) != cudaSuccess) rc = 1;
+  if (!rc) {
+    math_check<<<(n + 255) / 256, 256>>>(fn, n, d, d + n, d + 2 * (size_t)n);
+    if (cudaGetLastError() != cudaSuccess) rc = 1;
+  }
+  if (!rc && cudaMemcpy(ours, d + n, sizeof(float) * n, cudaMemcpyDeviceToHost) != cudaSuccess) rc = 1;
+  if (!rc && cudaMemcpy(ref, d + 2 * (size_t)n, sizeof(float) * n, cudaMemcpyDeviceToHost) != cudaSuccess) rc = 1;
+  cudaFree(d);
+  return rc;
 }

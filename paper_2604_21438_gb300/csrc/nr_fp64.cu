@@ -6,22 +6,18 @@
 
 namespace sfc {
 
-template <int TPB>
-__global__ void __launch_bounds__(TPB) sfchem_nr_fp64(KArgs a) {
-  li_persistent_body<double, false, true>(a);
-}
+// One kernel for every launch shape (64 or 128 threads per CTA).
+__global__ void __launch_bounds__(128) sfchem_nr_fp64(KArgs a) { li_persistent_body<double, false, true>(a); }
 
 cudaError_t launch_nr_fp64(const KArgs &a, int grid, int tpb, cudaStream_t s) {
-  if (tpb == 256) sfchem_nr_fp64<256><<<grid, 256, 0, s>>>(a);
-  else if (tpb == 64) sfchem_nr_fp64<64><<<grid, 64, 0, s>>>(a);
-  else sfchem_nr_fp64<128><<<grid, 128, 0, s>>>(a);
+  if (tpb != 64 && tpb != 128) return cudaErrorInvalidValue;
+  sfchem_nr_fp64<<<grid, tpb, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t occupancy_nr_fp64(int tpb, int *ctas_per_sm) {
-  if (tpb == 256) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, sfchem_nr_fp64<256>, 256, 0);
-  if (tpb == 64) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, sfchem_nr_fp64<64>, 64, 0);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, sfchem_nr_fp64<128>, 128, 0);
+  if (tpb != 64 && tpb != 128) return cudaErrorInvalidValue;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, sfchem_nr_fp64, tpb, 0);
 }
 
 }  // namespace sfc

@@ -73,6 +73,15 @@ struct sfchem_ctx {
   cudaGraphExec_t gexec;
   GraphKey gkey;
   bool have_graph;
+  // host-buffer pipeline: two copy streams, two device staging slots
+  bool have_pipe;
+  cudaStream_t s_in, s_out;
+  cudaEvent_t ev_start, ev_end, ev_in[2], ev_comp[2], ev_free[2];
+  void *stage_mem;
+  int64_t stage_cap;            // cells per slot
+  double *stage_f[2][12];       // n_H, T_g, T_d, E_IR, y_H2, y_e, G0, n_EUV, N_H2, y_H, y_H+, y_H-
+  int32_t *stage_nsub[2];
+  uint8_t *stage_status[2];
 };
 
 // ------------------------------------------------------------- schedule
@@ -136,7 +145,8 @@ sfchem_schedule(const int64_t *block_offset, float *block_cost, int32_t n_blocks
     }
     const int first = running + scan[threadIdx.x] - cnt;
     if (i < n_blocks) {
-      const int64_t s0 = block_offset[b], sz = block_offset[b + 1] - s0;
+      // cell index relative to the first block passed (0 for a whole layout)
+      const int64_t s0 = block_offset[b] - block_offset[0], sz = block_offset[b + 1] - block_offset[b];
       for (int c = 0; c < cnt; ++c) {
         ch_start[first + c] = s0 + (int64_t)c * chunk;
         ch_count[first + c] = (int32_t)min((int64_t)chunk, sz - (int64_t)c * chunk);
@@ -351,6 +361,38 @@ int batched_launch(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_fi
   return SFCHEM_OK;
 }
 
+// Streams, events and staging slots of the host-buffer pipeline (created on
+// first use, slots grown to `cells` cells each).
+int ensure_pipeline(sfchem_ctx *ctx, int64_t cells) {
+  if (!ctx->have_pipe) {
+    SFC_CUDA(cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
+    SFC_CUDA(cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
+    cudaEvent_t *evs[8] = {&ctx->ev_start, &ctx->ev_end, &ctx->ev_in[0], &ctx->ev_in[1], &ctx->ev_comp[0],
+                           &ctx->ev_comp[1], &ctx->ev_free[0], &ctx->ev_free[1]};
+    for (cudaEvent_t *e : evs) SFC_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    ctx->have_pipe = true;
+  }
+  if (cells > ctx->stage_cap) {
+    cudaFree(ctx->stage_mem);
+    ctx->stage_mem = nullptr;
+    ctx->stage_cap = 0;
+    // per slot: 12 double arrays, one int32 and one uint8 array, each start
+    // rounded up to 256 bytes
+    const size_t nd = ((size_t)cells * 8 + 255) / 256 * 256, ni = ((size_t)cells * 4 + 255) / 256 * 256,
+                 nb = ((size_t)cells + 255) / 256 * 256;
+    const size_t slot = 12 * nd + ni + nb;
+    SFC_CUDA(cudaMalloc(&ctx->stage_mem, 2 * slot));
+    for (int k = 0; k < 2; ++k) {
+      char *base = static_cast<char *>(ctx->stage_mem) + k * slot;
+      for (int j = 0; j < 12; ++j) ctx->stage_f[k][j] = reinterpret_cast<double *>(base + j * nd);
+      ctx->stage_nsub[k] = reinterpret_cast<int32_t *>(base + 12 * nd);
+      ctx->stage_status[k] = reinterpret_cast<uint8_t *>(base + 12 * nd + ni);
+    }
+    ctx->stage_cap = cells;
+  }
+  return SFCHEM_OK;
+}
+
 }  // namespace
 
 // ====================================================================== ABI
@@ -496,11 +538,109 @@ int sfchem_step_batched(sfchem_ctx *ctx, const sfchem_state_t *state, const sfch
   return SFCHEM_OK;
 }
 
+int sfchem_step_host(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_fields_t *fields,
+                     const int64_t *block_offset, const double *block_dt, int32_t n_blocks, double cd_factor,
+                     int64_t slice_cells, void *stream) {
+  if (int rc = check_ctx(ctx)) return rc;
+  if (!(std::isfinite(cd_factor) && cd_factor > 0.0) || slice_cells < 0) return SFCHEM_EINVAL;
+  if (int rc = check_arrays(state, fields)) return rc;
+  Shape sh;
+  if (int rc = resolve_shape(ctx, sh)) return rc;
+  int64_t ncells = 0, nch = 0;
+  if (int rc = check_blocks(block_offset, block_dt, n_blocks, sh.chunk, &ncells, &nch)) return rc;
+  if (n_blocks == 0 || ncells == 0) return SFCHEM_OK;
+  if (slice_cells == 0) slice_cells = SFCHEM_HOST_SLICE_DEFAULT;
+  // slices: runs of whole consecutive blocks of at most slice_cells cells
+  // (a larger block is a slice of its own)
+  std::vector<int32_t> cut(1, 0);
+  int64_t max_slice = 0;
+  for (int32_t b = 0; b < n_blocks;) {
+    int32_t e = b + 1;
+    while (e < n_blocks && block_offset[e + 1] - block_offset[b] <= slice_cells) ++e;
+    max_slice = std::max(max_slice, block_offset[e] - block_offset[b]);
+    cut.push_back(e);
+    b = e;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (int rc = sync_schedule(ctx, block_offset, block_dt, n_blocks, sh.chunk, (int32_t)nch, s)) return rc;
+  if (int rc = ensure_pipeline(ctx, max_slice)) return rc;
+  const double *in_h[9] = {state->n_H, state->T_gas, state->T_dust, state->E_IR, state->y_H2, state->y_e,
+                           fields->G0_fuv, fields->n_euv, fields->N_H2};
+  double *out_h[8] = {state->T_gas, state->T_dust, state->E_IR, state->y_H2, state->y_e,
+                      state->y_H, state->y_Hp, state->y_Hm};
+  const int out_j[8] = {1, 2, 3, 4, 5, 9, 10, 11};
+  // the copies are ordered after the work already queued on `stream`
+  SFC_CUDA(cudaEventRecord(ctx->ev_start, s));
+  SFC_CUDA(cudaStreamWaitEvent(ctx->s_in, ctx->ev_start, 0));
+  SFC_CUDA(cudaStreamWaitEvent(ctx->s_out, ctx->ev_start, 0));
+  const size_t smem = (sizeof(float) + sizeof(int32_t)) * SCHED_SORT_MAX;
+  for (size_t i = 0; i + 1 < cut.size(); ++i) {
+    const int k = (int)(i & 1);
+    const int32_t b0 = cut[i], b1 = cut[i + 1], nb = b1 - b0;
+    const int64_t c0 = block_offset[b0], nc = block_offset[b1] - c0;
+    int64_t chunks = 0;
+    for (int32_t b = b0; b < b1; ++b) chunks += (block_offset[b + 1] - block_offset[b] + sh.chunk - 1) / sh.chunk;
+    // in: wait until slot k's previous results are home, then copy the inputs
+    if (i >= 2) SFC_CUDA(cudaStreamWaitEvent(ctx->s_in, ctx->ev_free[k], 0));
+    for (int j = 0; j < 9; ++j)
+      SFC_CUDA(cudaMemcpyAsync(ctx->stage_f[k][j], in_h[j] + c0, sizeof(double) * nc, cudaMemcpyHostToDevice,
+                               ctx->s_in));
+    SFC_CUDA(cudaEventRecord(ctx->ev_in[k], ctx->s_in));
+    // compute on `stream`: the slice's chunk table, then the solver
+    SFC_CUDA(cudaStreamWaitEvent(s, ctx->ev_in[k], 0));
+    sfchem_state_t st;
+    std::memset(&st, 0, sizeof(st));
+    double *const *f = ctx->stage_f[k];
+    st.n_H = f[0]; st.T_gas = f[1]; st.T_dust = f[2]; st.E_IR = f[3]; st.y_H2 = f[4]; st.y_e = f[5];
+    st.y_H = state->y_H ? f[9] : nullptr;
+    st.y_Hp = state->y_Hp ? f[10] : nullptr;
+    st.y_Hm = state->y_Hm ? f[11] : nullptr;
+    st.status = state->status ? ctx->stage_status[k] : nullptr;
+    st.n_sub = state->n_sub ? ctx->stage_nsub[k] : nullptr;
+    sfchem_fields_t fl;
+    fl.G0_fuv = f[6]; fl.n_euv = f[7]; fl.N_H2 = f[8];
+    KArgs a = base_args(ctx, &st, &fl, cd_factor);
+    a.n_cells = nc;
+    a.chunk = sh.chunk;
+    a.n_chunks = (int32_t)chunks;
+    a.ch_start = ctx->d_ch_start; a.ch_count = ctx->d_ch_count; a.ch_block = ctx->d_ch_block;
+    a.block_dt = ctx->d_block_dt + b0;
+    a.block_cost = ctx->d_block_cost + b0;
+    if (i == 0) SFC_CUDA(cudaEventRecord(ctx->ev0, s));
+    SFC_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), s));
+    sfchem_schedule<<<1, SCHED_THREADS, nb <= SCHED_SORT_MAX ? smem : 0, s>>>(
+        ctx->d_block_offset + b0, ctx->d_block_cost + b0, nb, sh.chunk, ctx->d_ch_start, ctx->d_ch_count,
+        ctx->d_ch_block);
+    SFC_CUDA(cudaGetLastError());
+    SFC_CUDA(launch_solver(ctx, a, sh, s));
+    if (i + 2 == cut.size()) SFC_CUDA(cudaEventRecord(ctx->ev1, s));
+    SFC_CUDA(cudaEventRecord(ctx->ev_comp[k], s));
+    // out: copy the results home, then free slot k
+    SFC_CUDA(cudaStreamWaitEvent(ctx->s_out, ctx->ev_comp[k], 0));
+    for (int j = 0; j < 8; ++j)
+      if (out_h[j])
+        SFC_CUDA(cudaMemcpyAsync(out_h[j] + c0, f[out_j[j]], sizeof(double) * nc, cudaMemcpyDeviceToHost,
+                                 ctx->s_out));
+    if (state->status)
+      SFC_CUDA(cudaMemcpyAsync(state->status + c0, ctx->stage_status[k], nc, cudaMemcpyDeviceToHost, ctx->s_out));
+    if (state->n_sub)
+      SFC_CUDA(cudaMemcpyAsync(state->n_sub + c0, ctx->stage_nsub[k], sizeof(int32_t) * nc,
+                               cudaMemcpyDeviceToHost, ctx->s_out));
+    SFC_CUDA(cudaEventRecord(ctx->ev_free[k], ctx->s_out));
+  }
+  SFC_CUDA(cudaEventRecord(ctx->ev_end, ctx->s_out));
+  SFC_CUDA(cudaStreamWaitEvent(s, ctx->ev_end, 0));
+  SFC_CUDA(cudaStreamSynchronize(s));
+  ctx->timed = true;
+  ctx->calls++;
+  return SFCHEM_OK;
+}
+
 int sfchem_set_launch(sfchem_ctx *ctx, const sfchem_launch_t *launch) {
   if (int rc = check_ctx(ctx)) return rc;
   if (!launch) { std::memset(&ctx->launch, 0, sizeof(ctx->launch)); return SFCHEM_OK; }
   const int t = launch->threads_per_cta;
-  if (!(t == 0 || t == 64 || t == 128 || t == 256)) return SFCHEM_EINVAL;
+  if (!(t == 0 || t == 64 || t == 128)) return SFCHEM_EINVAL;
   if (launch->ctas_per_sm < 0 || launch->chunk < 0 || (launch->chunk % 32) != 0 || launch->chunk > 4096 ||
       launch->reserved)
     return SFCHEM_EINVAL;
@@ -545,10 +685,10 @@ int sfchem_autotune(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_f
   cudaError_t e = cudaMemcpyAsync(&saved_stats, ctx->d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, s);
   float best_ms = 1e30f;
   sfchem_launch_t best = saved;
-  const int tpbs[3] = {64, 128, 256};
+  const int tpbs[2] = {64, 128};
   const int chunks[3] = {32, 64, 128};
   int rc = SFCHEM_OK;
-  for (int ti = 0; ti < 3 && e == cudaSuccess && !rc; ++ti) {
+  for (int ti = 0; ti < 2 && e == cudaSuccess && !rc; ++ti) {
     int occ = 0;
     e = ctx->cfg.precision == SFCHEM_MIXED ? occupancy_li_mixed(tpbs[ti], &occ) : occupancy_li_fp64(tpbs[ti], &occ);
     if (e != cudaSuccess) break;
@@ -637,6 +777,14 @@ int sfchem_finalize(sfchem_ctx *ctx) {
   cudaEventDestroy(ctx->ev0);
   cudaEventDestroy(ctx->ev1);
   cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->have_pipe) {
+    cudaStreamDestroy(ctx->s_in);
+    cudaStreamDestroy(ctx->s_out);
+    cudaEvent_t evs[8] = {ctx->ev_start, ctx->ev_end, ctx->ev_in[0], ctx->ev_in[1], ctx->ev_comp[0],
+                          ctx->ev_comp[1], ctx->ev_free[0], ctx->ev_free[1]};
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
+  }
+  cudaFree(ctx->stage_mem);
   ctx->magic = 0;
   delete ctx;
   return SFCHEM_OK;
