@@ -194,6 +194,37 @@ template <typename W> struct CellK {
 template <typename W>
 __device__ __forceinline__ void make_cellk(CellK<W> &c, double n, double G0, double nEUV, double NH2,
                                            double cd_factor, double dt_h, const DevCfg &cfg) {
+  if constexpr (sizeof(W) == sizeof(float)) {
+    // Mixed path: the same constants in FP32 from the rounded inputs.  A lane
+    // computes them alone when its warp refills it with a new cell, and an
+    // FP64 warp instruction occupies the FP64 pipe whatever its number of
+    // active lanes: in FP64 these ~160 instructions per cell cost more pipe
+    // time than the substeps of a cell that needs a few dozen.
+    typedef M<float> m;
+    const float nf = d2f_int(n), G0f = d2f_int(G0), nEf = d2f_int(nEUV), NH2f = d2f_int(NH2);
+    const float Z = d2f_int(cfg.Z), Cd = d2f_int(cd_factor) * float(CD_UNIT);
+    c.n = nf;
+    c.rho = nf * float(MUH * MH);
+    c.fd = Z;
+    c.Cd = Cd;
+    c.EUV = (cfg.pmask & P_UV) ? float(CLIGHT * (SIG_DUV / (MUH * MH))) * (G0f * float(U_HAB) + nEf * float(HNU_EUV))
+                               : 0.0f;
+    c.k9 = ((cfg.rmask >> 9) & 1u) ? float(CLIGHT * SIG_EUV) * nEf : 0.0f;
+    // (N_H2 / N_0)^-3/4 as 1 / (sqrt(x) sqrt(sqrt(x))): a few ulp, where
+    // exp(-0.75 ln x) would carry the rounding of ln x (up to 5e-7)
+    static_assert(SH_POW == 0.75, "the FP32 shielding factor assumes the exponent 3/4");
+    const float xs = NH2f * float(1.0 / NSH0), sq = m::sqrt(xs);
+    const float fsh = NH2f > float(NSH0) ? m::rcp(sq * m::sqrt(sq)) : 1.0f;
+    c.k10 = ((cfg.rmask >> 10) & 1u) ? float(K_LW) * G0f * fsh : 0.0f;
+    c.k11 = ((cfg.rmask >> 11) & 1u) ? float(ZETA_CR) : 0.0f;
+    c.Gpre = (cfg.pmask & P_GG) ? nf * float(RG * 0.031622776601683794) : 0.0f;   // RG n / sqrt(T_high)
+    c.pe = (cfg.pmask & P_G4) ? float(PE_K) * G0f * Z : 0.0f;
+    c.lnn = m::log(nf);
+    c.rn = m::rcp(nf);
+    c.rCd = m::rcp(Cd);
+    c.dt_h = dt_h;
+    return;
+  }
   c.n = W(n);
   c.rho = W(MUH * MH * n);
   c.fd = W(cfg.Z);

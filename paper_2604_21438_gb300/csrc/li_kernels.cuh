@@ -114,6 +114,28 @@ __device__ __forceinline__ void lu5_solve(const LU5<W> &L, V b[5]) {
 template <typename W> __device__ __forceinline__ W m_abs(W x) { return M<W>::abs(x); }
 
 // ----------------------------------------------------------- projection
+// max(x, lo) and min(x, hi) of FP64 values against bounds lo >= +0 and
+// hi > 0 on the bit patterns: a non-negative double orders like its bits read
+// as a signed 64-bit integer, and a negative one (sign bit set) below every
+// non-negative bound.  Integer instructions only; equal to fmax / fmin for
+// every value but NaN, which they pass through.
+__device__ __forceinline__ double max_bits(double x, double lo) {
+  return __double_as_longlong(x) < __double_as_longlong(lo) ? lo : x;
+}
+__device__ __forceinline__ double min_bits(double x, double hi) {
+  return __double_as_longlong(x) > __double_as_longlong(hi) ? hi : x;
+}
+
+// project() with the constant bounds applied on the bit patterns: FP64
+// arithmetic only for the bound (1 - y_e)/2 of y_H2.
+__device__ __forceinline__ void project_bits(double u[5]) {
+  u[1] = min_bits(max_bits(u[1], 0.0), 1.0);
+  u[0] = fmin(max_bits(u[0], 0.0), (1.0 - u[1]) * 0.5);
+  u[2] = max_bits(u[2], TCMB);
+  u[3] = max_bits(u[3], TCMB);
+  u[4] = max_bits(u[4], EFLOOR);
+}
+
 // Positivity and conservation after an update: 0 <= y_e <= 1,
 // 0 <= y_H2 <= (1 - y_e)/2 (so y_H = 1 - 2 y_H2 - y_e >= 0), temperatures at
 // least T_CMB, E_IR at least the CMB-equivalent energy density.  FP64.
@@ -203,10 +225,8 @@ __device__ __forceinline__ int newton_dust_w(double u[5], W T, W Tb, W Eb, W g3,
     u[3] = fmax(u[3], TCMB);
     u[4] = fmax(u[4], EFLOOR);
   } else {
-    // the W iterate is already clamped: the FP64 floors can only act when
-    // it lies within W rounding of them
-    if (!(Tb + a3 > W(TCMB * 1.001))) u[3] = fmax(u[3], TCMB);
-    if (!(Eb + a4 > W(EFLOOR * 1.001))) u[4] = fmax(u[4], EFLOOR);
+    u[3] = max_bits(u[3], TCMB);
+    u[4] = max_bits(u[4], EFLOOR);
   }
   return result;
 }
@@ -228,16 +248,29 @@ template <typename W> struct CellRun {
   int8_t mode;   // -1 undecided, 0 subcycling, 1 tight coupling
 };
 
+// Input checks on the bit patterns (integer instructions; a lane runs them
+// alone when its warp refills it): finite, n_H, T_g, T_d > 0, the others >= 0
+// (-0 included), y_e <= 1; only the H-nuclei budget 2 y_H2 + y_e <= 1 + 1e-9
+// takes FP64 arithmetic.
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff;
+}
+__device__ __forceinline__ bool positive_bits(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool nonneg_bits(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 || b == (long long)0x8000000000000000ULL;
+}
 __device__ __forceinline__ bool valid_input(double n, double Tg, double Td, double E, double y2,
                                             double ye, double G0, double nE, double NH2, double dt) {
   const double v[10] = {n, Tg, Td, E, y2, ye, G0, nE, NH2, dt};
+  bool ok = true;
 #pragma unroll
-  for (int i = 0; i < 10; ++i)
-    if (!isfinite(v[i])) return false;
-  if (!(n > 0.0 && Tg > 0.0 && Td > 0.0 && E >= 0.0 && y2 >= 0.0 && ye >= 0.0 && ye <= 1.0)) return false;
-  if (!(2.0 * y2 + ye <= 1.0 + 1e-9)) return false;
-  if (!(G0 >= 0.0 && nE >= 0.0 && NH2 >= 0.0 && dt >= 0.0)) return false;
-  return true;
+  for (int i = 0; i < 10; ++i) ok = ok && finite_bits(v[i]);
+  ok = ok && positive_bits(n) && positive_bits(Tg) && positive_bits(Td);
+  ok = ok && nonneg_bits(E) && nonneg_bits(y2) && nonneg_bits(ye) && nonneg_bits(G0) && nonneg_bits(nE) &&
+       nonneg_bits(NH2) && nonneg_bits(dt);
+  ok = ok && __double_as_longlong(ye) <= __double_as_longlong(1.0);
+  return ok && 2.0 * y2 + ye <= 1.0 + 1e-9;
 }
 
 // Residual of the factored FP32 system, r = b - A x, formed to about twice
@@ -382,19 +415,22 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
   c.u[3] = fma(c.u[3], to_f64(x[3]), c.u[3]);
   c.u[4] = fma(c.u[4], to_f64(x[4]), c.u[4]);
   if constexpr (MIXED) {
-    // The projection only changes a value that reached a bound.  A W-precision
-    // estimate of the new state decides, with a safety margin far above its
-    // rounding error, whether any bound can be active; only then the FP64
-    // projection runs (it is the identity otherwise).
+    // The projection of project() without the FP64 pipe where the bound is
+    // a constant (integer clamps on the bit patterns, the same values).  Only
+    // y_H2 <= (1 - y_e)/2 needs FP64 arithmetic; a W-precision estimate of the
+    // new state, with a margin far above its rounding error, decides whether
+    // it can bind.  (As one FP64 branch for all bounds, the projection ran in
+    // most warps for a few of their lanes, and an FP64 warp instruction
+    // occupies the pipe whatever its number of active lanes.)
+    c.u[1] = min_bits(max_bits(c.u[1], 0.0), 1.0);
+    c.u[0] = max_bits(c.u[0], 0.0);
+    c.u[2] = max_bits(c.u[2], TCMB);
+    c.u[3] = max_bits(c.u[3], TCMB);
+    c.u[4] = max_bits(c.u[4], EFLOOR);
     const W y2n = S.uf[0] + x[0] + dx[0], yen = S.uf[1] + x[1] + dx[1];
     const W e2 = W(1e-4) * (m_abs(S.uf[0]) + m_abs(x[0]) + m_abs(dx[0]));
     const W ee = W(1e-4) * (m_abs(S.uf[1]) + m_abs(x[1]) + m_abs(dx[1]));
-    const bool inside = (y2n > e2) && (yen > ee) && (yen < W(1) - ee - W(1e-6)) &&
-                        (y2n + e2 < (W(1) - yen - ee) * W(0.5) - W(1e-6)) &&
-                        (S.uf[2] * (W(1) + x[2]) > W(TCMB * 1.001)) &&
-                        (S.uf[3] * (W(1) + x[3]) > W(TCMB * 1.001)) &&
-                        (S.uf[4] * (W(1) + x[4]) > W(EFLOOR * 1.001));
-    if (!inside) project(c.u);
+    if (!(y2n + e2 < (W(1) - yen - ee) * W(0.5) - W(1e-6))) c.u[0] = fmin(c.u[0], (1.0 - c.u[1]) * 0.5);
   } else {
     project(c.u);
   }
@@ -436,7 +472,7 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
 template <typename W>
 __device__ __forceinline__ double y_hminus(double Td, double ye) {
   typedef M<W> m;
-  const W T = W(Td);
+  const W T = to_w<W>(Td);
   const W lnT = m::log(T);
   const W k2 = m::exp(W(-41.11005943727161) + W(0.928) * lnT - T * W(1.0 / 16200.0));
   const W N = m::exp(W(0.098493) * lnT) + W(0.32852) * m::exp(W(0.5561) * lnT) +
@@ -444,7 +480,7 @@ __device__ __forceinline__ double y_hminus(double Td, double ye) {
   const W D = W(1) + W(6.191e-3) * m::exp(W(1.0461) * lnT) + W(8.9712e-11) * m::exp(W(3.0424) * lnT) +
               W(3.2576e-14) * m::exp(W(3.7741) * lnT);
   const W k3 = W(1.35e-9) * N / D;
-  return double(k2 / k3) * ye;
+  return to_f64(k2 / k3) * ye;
 }
 
 // ------------------------------------------------------------ the kernel
@@ -545,7 +581,8 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
           if (a.nsub) a.nsub[idx] = 0;
         } else {
           make_cellk<W>(c.k, n, G0, nE, NH2, a.cd_factor, cdt, cfg);
-          project(c.u);
+          if constexpr (MIXED) project_bits(c.u);
+          else project(c.u);
           have = true;
           if (cdt == 0.0) have = false;   // nothing to integrate: store the projected state
           if (!have) {
