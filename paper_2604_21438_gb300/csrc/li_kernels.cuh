@@ -240,7 +240,7 @@ __device__ __forceinline__ int newton_dust(double u[5], const double u0[5], doub
 // ------------------------------------------------------------- one cell
 template <typename W> struct CellRun {
   double u[5];   // y_H2, y_e, T_g, T_d, E_IR
-  double t;      // time advanced so far in this call
+  double t;      // time advanced so far in this call (mixed LI path: time left)
   CellK<W> k;
   int32_t nsub, nitr;
   int32_t nri, ntries;   // halving exponent of the step (both methods); NR attempts
@@ -314,7 +314,9 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
   if (c.mode == 0) inv = fmax_w(inv, S.rate_dust);
   const W dtcw = cw.f_chem / inv;                   // +inf when every rate vanishes
   const double dtc = to_f64(dtcw);
-  const double rem = dt_h - c.t;
+  // time left: the FP64 path keeps the elapsed time (the oracle's order of
+  // operations), the mixed path the time left itself (one FP64 add less)
+  const double rem = MIXED ? c.t : dt_h - c.t;
   // c.nri > 0: the update of this substep was rejected c.nri times (below)
   // and is redone with the step halved as often (exact powers of two)
   bool fits;
@@ -461,7 +463,8 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
     if (it < 0) { c.st |= ST_NOCONV; it = -it; }
     c.nitr += it;
   }
-  c.t = last ? dt_h : c.t + dts;
+  if constexpr (MIXED) c.t = last ? 0.0 : rem - dts;
+  else c.t = last ? dt_h : c.t + dts;
   c.nsub++;
   if (last) return true;
   if (c.nsub >= cfg.n_sub_max) { c.st |= ST_CAP; return true; }
@@ -569,7 +572,7 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
         const double n = __ldg(a.nH + idx), G0 = __ldg(a.G0 + idx), nE = __ldg(a.nEUV + idx),
                      NH2 = __ldg(a.NH2 + idx);
         c.u[0] = a.y2[idx]; c.u[1] = a.ye[idx]; c.u[2] = a.Tg[idx]; c.u[3] = a.Td[idx]; c.u[4] = a.E[idx];
-        c.t = 0.0; c.nsub = 0; c.nitr = 0; c.nri = 0; c.ntries = 0; c.st = 0; c.mode = -1;
+        c.t = (MIXED && !NR) ? cdt : 0.0; c.nsub = 0; c.nitr = 0; c.nri = 0; c.ntries = 0; c.st = 0; c.mode = -1;
         s_cells++;
         if (!valid_input(n, c.u[2], c.u[3], c.u[4], c.u[0], c.u[1], G0, nE, NH2, cdt)) {
           c.st = ST_BAD;

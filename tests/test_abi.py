@@ -54,6 +54,8 @@ def test_host_rejections_before_any_launch():
     assert L.sfchem_stats(None, None) == sf.ENOTINIT
     assert L.sfchem_finalize(None) == sf.ENOTINIT
     assert L.sfchem_step_batched(None, None, None, None, None, 0, 1.0, None) == sf.ENOTINIT
+    assert L.sfchem_step_host(None, None, None, None, None, 0, 1.0, 0, None) == sf.ENOTINIT
+    assert L.sfchem_step_nr(None, ctypes.byref(st), ctypes.byref(fl), 10, 1.0, 1.0, None) == sf.ENOTINIT
 
 
 def test_strerror_and_version():
