@@ -212,19 +212,22 @@ int sfchem_step_batched(sfchem_ctx *ctx, const sfchem_state_t *state,
  * the paper, whose solver runs on device-resident hydro data; this is the
  * call for a caller whose cells live on the host).  The blocks are cut into
  * slices of consecutive whole blocks of at most slice_cells cells (0: the
- * default below; a larger block is a slice of its own); while slice i is
- * solved on `stream`, the inputs of slice i+1 are copied to the device and
- * the results of slice i-1 back to the host on two library-owned streams,
- * through two library-owned device staging slots (grown on demand to the
- * largest slice: 101 bytes per cell each).  All arrays of state and fields
- * are host arrays of block_offset[n_blocks] entries (pinned memory gives
- * asynchronous copies; pageable memory works, copied synchronously by the
- * driver); optional outputs (y_H, y_Hp, y_Hm, status, n_sub) may be NULL and
- * are then neither computed into nor copied.  The work is ordered after the
- * work already queued on `stream`, and the call returns when every result
- * is in host memory (it synchronizes `stream`).  Errors as
- * sfchem_step_batched; slice_cells < 0 is SFCHEM_EINVAL. */
-#define SFCHEM_HOST_SLICE_DEFAULT 2097152
+ * default below; a larger block is a slice of its own; the first and the
+ * last slice take a quarter of it, since their copies overlap no solver
+ * work).  While slice i is solved, the inputs of slice i+1 are copied to the
+ * device and the results of slice i-1 back to the host; the solvers of
+ * consecutive slices overlap.  The library owns the streams (copy-in,
+ * copy-out, one compute stream per slot) and two device staging slots (each
+ * grown on demand to the largest slice: 101 bytes per cell, plus its chunk
+ * table).  All arrays of state and fields are host arrays of
+ * block_offset[n_blocks] entries (pinned memory gives asynchronous copies;
+ * pageable memory works, copied synchronously by the driver); optional
+ * outputs (y_H, y_Hp, y_Hm, status, n_sub) may be NULL and are then neither
+ * computed into nor copied.  The work is ordered after the work already
+ * queued on `stream`, and the call returns when every result is in host
+ * memory (it synchronizes `stream`).  Errors as sfchem_step_batched;
+ * slice_cells < 0 is SFCHEM_EINVAL. */
+#define SFCHEM_HOST_SLICE_DEFAULT 4194304
 int sfchem_step_host(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_fields_t *fields,
                      const int64_t *block_offset, const double *block_dt, int32_t n_blocks,
                      double cd_factor, int64_t slice_cells, void *stream);

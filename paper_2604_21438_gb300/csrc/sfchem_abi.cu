@@ -73,15 +73,22 @@ struct sfchem_ctx {
   cudaGraphExec_t gexec;
   GraphKey gkey;
   bool have_graph;
-  // host-buffer pipeline: two copy streams, two device staging slots
+  // host-buffer pipeline: a copy-in and a copy-out stream, and per staging
+  // slot a compute stream, a work counter and a chunk table, so that the
+  // solver of one slice runs while the previous one drains its last cells
   bool have_pipe;
-  cudaStream_t s_in, s_out;
+  cudaStream_t s_in, s_out, s_comp[2];
   cudaEvent_t ev_start, ev_end, ev_in[2], ev_comp[2], ev_free[2];
   void *stage_mem;
   int64_t stage_cap;            // cells per slot
   double *stage_f[2][12];       // n_H, T_g, T_d, E_IR, y_H2, y_e, G0, n_EUV, N_H2, y_H, y_H+, y_H-
   int32_t *stage_nsub[2];
   uint8_t *stage_status[2];
+  void *pipe_tab;
+  int64_t pipe_tab_cap;         // chunks per slot
+  unsigned long long *pipe_counter[2];
+  int64_t *pipe_ch_start[2];
+  int32_t *pipe_ch_count[2], *pipe_ch_block[2];
 };
 
 // ------------------------------------------------------------- schedule
@@ -363,10 +370,12 @@ int batched_launch(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_fi
 
 // Streams, events and staging slots of the host-buffer pipeline (created on
 // first use, slots grown to `cells` cells each).
-int ensure_pipeline(sfchem_ctx *ctx, int64_t cells) {
+int ensure_pipeline(sfchem_ctx *ctx, int64_t cells, int64_t chunks) {
   if (!ctx->have_pipe) {
     SFC_CUDA(cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
     SFC_CUDA(cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
+    SFC_CUDA(cudaStreamCreateWithFlags(&ctx->s_comp[0], cudaStreamNonBlocking));
+    SFC_CUDA(cudaStreamCreateWithFlags(&ctx->s_comp[1], cudaStreamNonBlocking));
     cudaEvent_t *evs[8] = {&ctx->ev_start, &ctx->ev_end, &ctx->ev_in[0], &ctx->ev_in[1], &ctx->ev_comp[0],
                            &ctx->ev_comp[1], &ctx->ev_free[0], &ctx->ev_free[1]};
     for (cudaEvent_t *e : evs) SFC_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
@@ -389,6 +398,23 @@ int ensure_pipeline(sfchem_ctx *ctx, int64_t cells) {
       ctx->stage_status[k] = reinterpret_cast<uint8_t *>(base + 12 * nd + ni);
     }
     ctx->stage_cap = cells;
+  }
+  if (chunks > ctx->pipe_tab_cap) {
+    cudaFree(ctx->pipe_tab);
+    ctx->pipe_tab = nullptr;
+    ctx->pipe_tab_cap = 0;
+    // per slot: counter, chunk starts (int64), counts and blocks (int32)
+    const size_t n8 = ((size_t)chunks * 8 + 255) / 256 * 256, n4 = ((size_t)chunks * 4 + 255) / 256 * 256;
+    const size_t slot = 256 + n8 + 2 * n4;
+    SFC_CUDA(cudaMalloc(&ctx->pipe_tab, 2 * slot));
+    for (int k = 0; k < 2; ++k) {
+      char *base = static_cast<char *>(ctx->pipe_tab) + k * slot;
+      ctx->pipe_counter[k] = reinterpret_cast<unsigned long long *>(base);
+      ctx->pipe_ch_start[k] = reinterpret_cast<int64_t *>(base + 256);
+      ctx->pipe_ch_count[k] = reinterpret_cast<int32_t *>(base + 256 + n8);
+      ctx->pipe_ch_block[k] = reinterpret_cast<int32_t *>(base + 256 + n8 + n4);
+    }
+    ctx->pipe_tab_cap = chunks;
   }
   return SFCHEM_OK;
 }
@@ -551,19 +577,29 @@ int sfchem_step_host(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_
   if (n_blocks == 0 || ncells == 0) return SFCHEM_OK;
   if (slice_cells == 0) slice_cells = SFCHEM_HOST_SLICE_DEFAULT;
   // slices: runs of whole consecutive blocks of at most slice_cells cells
-  // (a larger block is a slice of its own)
+  // (a larger block is a slice of its own).  The copy-in of the first slice
+  // and the copy-out of the last one overlap no solver work, so those two
+  // slices take a quarter of slice_cells.
   std::vector<int32_t> cut(1, 0);
-  int64_t max_slice = 0;
+  int64_t max_slice = 0, max_chunks = 0;
+  const int64_t total = block_offset[n_blocks], quarter = std::max<int64_t>(slice_cells / 4, 1);
   for (int32_t b = 0; b < n_blocks;) {
+    const int64_t left = total - block_offset[b];
+    int64_t target = slice_cells;
+    if (b == 0) target = quarter;
+    else if (left > quarter && left <= slice_cells + quarter) target = left - quarter;
     int32_t e = b + 1;
-    while (e < n_blocks && block_offset[e + 1] - block_offset[b] <= slice_cells) ++e;
+    while (e < n_blocks && block_offset[e + 1] - block_offset[b] <= target) ++e;
     max_slice = std::max(max_slice, block_offset[e] - block_offset[b]);
+    int64_t chunks = 0;
+    for (int32_t q = b; q < e; ++q) chunks += (block_offset[q + 1] - block_offset[q] + sh.chunk - 1) / sh.chunk;
+    max_chunks = std::max(max_chunks, chunks);
     cut.push_back(e);
     b = e;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (int rc = sync_schedule(ctx, block_offset, block_dt, n_blocks, sh.chunk, (int32_t)nch, s)) return rc;
-  if (int rc = ensure_pipeline(ctx, max_slice)) return rc;
+  if (int rc = ensure_pipeline(ctx, max_slice, max_chunks)) return rc;
   const double *in_h[9] = {state->n_H, state->T_gas, state->T_dust, state->E_IR, state->y_H2, state->y_e,
                            fields->G0_fuv, fields->n_euv, fields->N_H2};
   double *out_h[8] = {state->T_gas, state->T_dust, state->E_IR, state->y_H2, state->y_e,
@@ -571,8 +607,8 @@ int sfchem_step_host(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_
   const int out_j[8] = {1, 2, 3, 4, 5, 9, 10, 11};
   // the copies are ordered after the work already queued on `stream`
   SFC_CUDA(cudaEventRecord(ctx->ev_start, s));
-  SFC_CUDA(cudaStreamWaitEvent(ctx->s_in, ctx->ev_start, 0));
-  SFC_CUDA(cudaStreamWaitEvent(ctx->s_out, ctx->ev_start, 0));
+  cudaStream_t deps[4] = {ctx->s_in, ctx->s_out, ctx->s_comp[0], ctx->s_comp[1]};
+  for (cudaStream_t d : deps) SFC_CUDA(cudaStreamWaitEvent(d, ctx->ev_start, 0));
   const size_t smem = (sizeof(float) + sizeof(int32_t)) * SCHED_SORT_MAX;
   for (size_t i = 0; i + 1 < cut.size(); ++i) {
     const int k = (int)(i & 1);
@@ -586,8 +622,10 @@ int sfchem_step_host(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_
       SFC_CUDA(cudaMemcpyAsync(ctx->stage_f[k][j], in_h[j] + c0, sizeof(double) * nc, cudaMemcpyHostToDevice,
                                ctx->s_in));
     SFC_CUDA(cudaEventRecord(ctx->ev_in[k], ctx->s_in));
-    // compute on `stream`: the slice's chunk table, then the solver
-    SFC_CUDA(cudaStreamWaitEvent(s, ctx->ev_in[k], 0));
+    // compute on slot k's stream: the slice's chunk table, then the solver
+    // (it overlaps the end of the previous slice's solver on the other one)
+    cudaStream_t sc = ctx->s_comp[k];
+    SFC_CUDA(cudaStreamWaitEvent(sc, ctx->ev_in[k], 0));
     sfchem_state_t st;
     std::memset(&st, 0, sizeof(st));
     double *const *f = ctx->stage_f[k];
@@ -603,18 +641,18 @@ int sfchem_step_host(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_
     a.n_cells = nc;
     a.chunk = sh.chunk;
     a.n_chunks = (int32_t)chunks;
-    a.ch_start = ctx->d_ch_start; a.ch_count = ctx->d_ch_count; a.ch_block = ctx->d_ch_block;
+    a.ch_start = ctx->pipe_ch_start[k]; a.ch_count = ctx->pipe_ch_count[k]; a.ch_block = ctx->pipe_ch_block[k];
+    a.counter = ctx->pipe_counter[k];
     a.block_dt = ctx->d_block_dt + b0;
     a.block_cost = ctx->d_block_cost + b0;
-    if (i == 0) SFC_CUDA(cudaEventRecord(ctx->ev0, s));
-    SFC_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), s));
-    sfchem_schedule<<<1, SCHED_THREADS, nb <= SCHED_SORT_MAX ? smem : 0, s>>>(
-        ctx->d_block_offset + b0, ctx->d_block_cost + b0, nb, sh.chunk, ctx->d_ch_start, ctx->d_ch_count,
-        ctx->d_ch_block);
+    if (i == 0) SFC_CUDA(cudaEventRecord(ctx->ev0, sc));
+    SFC_CUDA(cudaMemsetAsync(ctx->pipe_counter[k], 0, sizeof(unsigned long long), sc));
+    sfchem_schedule<<<1, SCHED_THREADS, nb <= SCHED_SORT_MAX ? smem : 0, sc>>>(
+        ctx->d_block_offset + b0, ctx->d_block_cost + b0, nb, sh.chunk, ctx->pipe_ch_start[k],
+        ctx->pipe_ch_count[k], ctx->pipe_ch_block[k]);
     SFC_CUDA(cudaGetLastError());
-    SFC_CUDA(launch_solver(ctx, a, sh, s));
-    if (i + 2 == cut.size()) SFC_CUDA(cudaEventRecord(ctx->ev1, s));
-    SFC_CUDA(cudaEventRecord(ctx->ev_comp[k], s));
+    SFC_CUDA(launch_solver(ctx, a, sh, sc));
+    SFC_CUDA(cudaEventRecord(ctx->ev_comp[k], sc));
     // out: copy the results home, then free slot k
     SFC_CUDA(cudaStreamWaitEvent(ctx->s_out, ctx->ev_comp[k], 0));
     for (int j = 0; j < 8; ++j)
@@ -630,6 +668,7 @@ int sfchem_step_host(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_
   }
   SFC_CUDA(cudaEventRecord(ctx->ev_end, ctx->s_out));
   SFC_CUDA(cudaStreamWaitEvent(s, ctx->ev_end, 0));
+  SFC_CUDA(cudaEventRecord(ctx->ev1, s));
   SFC_CUDA(cudaStreamSynchronize(s));
   ctx->timed = true;
   ctx->calls++;
@@ -780,11 +819,14 @@ int sfchem_finalize(sfchem_ctx *ctx) {
   if (ctx->have_pipe) {
     cudaStreamDestroy(ctx->s_in);
     cudaStreamDestroy(ctx->s_out);
+    cudaStreamDestroy(ctx->s_comp[0]);
+    cudaStreamDestroy(ctx->s_comp[1]);
     cudaEvent_t evs[8] = {ctx->ev_start, ctx->ev_end, ctx->ev_in[0], ctx->ev_in[1], ctx->ev_comp[0],
                           ctx->ev_comp[1], ctx->ev_free[0], ctx->ev_free[1]};
     for (cudaEvent_t e : evs) cudaEventDestroy(e);
   }
   cudaFree(ctx->stage_mem);
+  cudaFree(ctx->pipe_tab);
   ctx->magic = 0;
   delete ctx;
   return SFCHEM_OK;
