@@ -458,3 +458,28 @@ def test_solve5_is_exact_on_badly_scaled_systems():
         x = rng.standard_normal(5) / d2
         b = d1 * (B @ (d2 * x))
         np.testing.assert_allclose(oracle.solve5(A, b), x, rtol=1e-10)
+
+
+# ------------------------------------------------------------ reading R30
+def test_step_rejection_keeps_updates_small():
+    """Reading of the small-change assumption behind Eq. eq_deq: an update
+    that would move y_H2 or y_e by more than half of max(y, y_floor), or T_g
+    by more than a factor 2, is redone with half the step.  On the GRF cell
+    that sits at an unstable thermal balance (the single LI update threw it
+    to T_CMB or 1.4e5 K depending on C_d), every recorded substep stays
+    inside those bounds and the result is the same physical state for
+    C_d = 1e4 and 1e7."""
+    g = inputs.cells_grf(128, seed=1002)
+    cell = {k: float(g[k][1024557]) for k in inputs.FIELDS}
+    cfg = oracle.default_config()
+    finals = []
+    for cd in (1.0, 1000.0):
+        rec, st = oracle.li_trace(cell, 1e3 * inputs.YR, cd, cfg)
+        u = np.array([[cell["y_H2"], cell["y_e"], cell["T_g"]]] + [r[2:5] for r in rec])
+        dy = np.abs(np.diff(u[:, :2], axis=0))
+        assert np.all(dy <= 0.5 * np.maximum(u[:-1, :2], cfg.y_floor) * (1 + 1e-12))
+        ratio = u[1:, 2] / u[:-1, 2]
+        assert np.all((ratio <= 2.0 + 1e-12) & (ratio >= 0.5 - 1e-12))
+        finals.append(rec[-1][4])
+        assert 10.0 < rec[-1][4] < 2e4
+    assert abs(finals[0] / finals[1] - 1.0) < 1e-3
