@@ -555,10 +555,13 @@ def run_sweep(args):
                 dev[k] = {"max": float(e.max()), "p99": float(np.percentile(e, 99)),
                           "median": float(np.median(e)), "frac_above_1e-3": float((e > 1e-3).mean())}
             ns = out["n_sub"]
+            edges = np.array([0, 1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 1 << 30])
             rows.append({"dt_yr": dt_yr, "cd_factor": cd, "C_d": cd * 1e4, "ms": ms,
                          "cell_updates_per_s": n / (ms * 1e-3),
                          "n_sub": {"mean": float(ns.mean()), "p50": float(np.median(ns)),
-                                   "p99": float(np.percentile(ns, 99)), "max": int(ns.max())},
+                                   "p99": float(np.percentile(ns, 99)), "max": int(ns.max()),
+                                   "hist_edges": edges.tolist(),
+                                   "hist": np.histogram(ns, bins=edges)[0].tolist()},
                          "tight_fraction": st["tight_cells"] / max(st["cells"], 1),
                          "newton_per_substep": st["newton_iters"] / max(st["substeps"], 1),
                          "deviation_from_cd1": dev})
