@@ -68,3 +68,16 @@ def err_summary(got, ref, small=1e-8, idx=None):
         e = np.where(np.abs(b) > small, np.abs(a - b) / np.maximum(np.abs(b), 1e-300), np.abs(a - b) / small)
         res[k] = dict(max=float(e.max()), p99=float(np.percentile(e, 99)), median=float(np.median(e)))
     return res
+
+
+# status bits that flag a cell (not the tight-coupling mode bit)
+FLAGGED = 1 | 2 | 4 | 16
+
+
+def sample_with_flagged(got, n_cells, n, seed):
+    """Sorted indices of a seeded sample of n cells plus every cell whose
+    GPU status carries a flag (substep cap, bad input, Newton limit, bad
+    step)."""
+    idx = np.random.default_rng(seed).choice(n_cells, min(n, n_cells), replace=False)
+    flagged = np.nonzero(got["status"] & FLAGGED)[0]
+    return np.unique(np.concatenate([idx, flagged]))
