@@ -304,6 +304,31 @@ def be_dt(levels: int = 3) -> float:
     return 0.5 * (6.45 / 32.0 / 2.0 ** (levels - 1)) / np.sqrt(4.0 * np.pi * G * 1.4 * mH * 1.2e4)
 
 
+def cells_extreme(n: int = 4096, seed: int = 2024) -> dict:
+    """Independent cells over ranges wider than any workload's, for
+    robustness tests: log n_H ~ U(-2, 12); log T_g ~ U(log 3, 5);
+    log T_d ~ U(log 3, log 3 + 3); y_e within 1e-8 of 1 for a fifth of the
+    cells, else log y_e ~ U(-10, 0); y_H2 within a factor 1 - 1e-8 of
+    (1 - y_e)/2 for 30 % of the cells, else U(0, 1) (1 - y_e)/2;
+    log G0 ~ U(-3, 6); log n_EUV ~ U(-8, 4); log N_H2 ~ U(12, 25);
+    E_IR = (c / c~) a T_d^4."""
+    rng = np.random.default_rng(seed)
+    u = rng.random((10, n))
+    c = {}
+    c["n_H"] = 10.0 ** (-2.0 + 14.0 * u[0])
+    c["T_g"] = 10.0 ** (np.log10(3.0) + (5.0 - np.log10(3.0)) * u[1])
+    c["T_d"] = 10.0 ** (np.log10(3.0) + 3.0 * u[2])
+    ye = np.where(u[3] < 0.2, 1.0 - 10.0 ** (-8.0 * u[4]), 10.0 ** (-10.0 + 10.0 * u[4]))
+    c["y_e"] = np.minimum(ye, 1.0)
+    half = (1.0 - c["y_e"]) / 2.0
+    c["y_H2"] = np.where(u[5] < 0.3, half * (1.0 - 10.0 ** (-8.0 * u[6])), u[6] * half)
+    c["G0"] = 10.0 ** (-3.0 + 9.0 * u[7])
+    c["n_EUV"] = 10.0 ** (-8.0 + 12.0 * u[8])
+    c["N_H2"] = 10.0 ** (12.0 + 13.0 * u[9])
+    c["E_IR"] = _e_ir(c["T_d"])
+    return _finish(c)
+
+
 def paper_case(case: int) -> dict:
     """One cell of the paper's chemistry tests (Sec. 3.5, Table chemistryTest)."""
     if case == 1:
