@@ -264,34 +264,57 @@ template <typename W> struct Rates {
 
 // Powers and reciprocals of T_g and T_d shared by the rate and cooling terms.
 template <typename W> struct Pre {
-  W lnT, rT, sqT, rsqT, rTd;
+  W lnT, lnT4, rT, sqT, rsqT, rTd;   // lnT4 = ln(T / 1e4), accurate near 1e4 K
 };
+
+// FP32: ln T is taken relative to 1e4 K, through log1p near it: the rates
+// that matter in ionized gas (H0, H1) are steep in T, and the absolute
+// rounding of ln T ~ 9.5 (half an ulp is 4.8e-7 in FP32) would move them by
+// up to |d ln k / d ln T| x 4.8e-7 (13.5 x for collisional ionization near
+// its threshold).  FP64 has the digits to spare and takes ln T directly.
+template <typename W>
+__device__ __forceinline__ void make_pre(W T, W Td, Pre<W> &q) {
+  typedef M<W> m;
+  if constexpr (sizeof(W) == sizeof(double)) {
+    q.lnT = m::log(T);
+    q.lnT4 = q.lnT - W(9.210340371976184);
+  } else {
+    const W t = T * W(1e-4);
+    q.lnT4 = (t > W(0.5) && t < W(2)) ? m::log1p(t - W(1)) : m::log(t);
+    q.lnT = q.lnT4 + W(9.210340371976184);
+  }
+  q.rT = m::rcp(T);
+  q.sqT = m::sqrt(T);
+  q.rsqT = m::rcp(q.sqT);
+  q.rTd = m::rcp(Td);
+}
 
 template <typename W>
 __device__ __forceinline__ void eval_rates(W T, W Td, const Pre<W> &q, const CellK<W> &c, uint32_t rmask,
                                            Rates<W> &r) {
   typedef M<W> m;
-  const W lnT = q.lnT, rT = q.rT;
+  const W lnT = q.lnT, lnT4 = q.lnT4, rT = q.rT;
   // H0: Abel et al. fit in ln T(eV)
   {
-    const W x = lnT - W(9.359148232903149);  // ln(11604.5)
-    const W a0 = W(-32.71396786), a1 = W(13.536556), a2 = W(-5.73932875), a3 = W(1.563154998),
+    const W x = lnT4 - W(0.14880786093196532);  // ln(T / 11604.5)
+    // a0 = -32.71396786 enters as exp(a0), outside the exponential below
+    const W a1 = W(13.536556), a2 = W(-5.73932875), a3 = W(1.563154998),
             a4 = W(-0.2877056), a5 = W(3.48255977e-2), a6 = W(-2.63197617e-3),
             a7 = W(1.11954395e-4), a8 = W(-2.03914985e-6);
     W p = a8;
     p = p * x + a7; p = p * x + a6; p = p * x + a5; p = p * x + a4;
-    p = p * x + a3; p = p * x + a2; p = p * x + a1; p = p * x + a0;
+    p = p * x + a3; p = p * x + a2; p = p * x + a1; p = p * x;   // minus a0
     W dp = W(8) * a8;
     dp = dp * x + W(7) * a7; dp = dp * x + W(6) * a6; dp = dp * x + W(5) * a5;
     dp = dp * x + W(4) * a4; dp = dp * x + W(3) * a3; dp = dp * x + W(2) * a2; dp = dp * x + a1;
-    r.k[0] = m::exp(p);
+    r.k[0] = W(6.201607514089056e-15) * m::exp(p);   // exp(a0) exp(p - a0): p - a0 is small near 1e4 K
     r.kT[0] = r.k[0] * dp;
   }
   // H1: case-B recombination
   {
-    const W X = m::exp(W(0.407) * (W(11.654320855151537) - lnT));      // (115188/T)^0.407
-    const W lnk = W(-31.22350007575617) + W(1.5) * (W(12.662275226919286) - lnT) - W(2.242) * m::log1p(X);
-    r.k[1] = m::exp(lnk);
+    const W X = m::exp(W(0.407) * (W(2.4439804831753538) - lnT4));      // (115188/T)^0.407
+    // the constant part of ln k taken out of the exponential (e^-26.0456)
+    r.k[1] = W(4.881357330013074e-12) * m::exp(W(-1.5) * lnT4 - W(2.242) * m::log1p(X));
     r.kT[1] = r.k[1] * (W(-1.5) + W(2.242 * 0.407) * X * m::rcp(W(1) + X));
   }
   // H2: H- formation
@@ -439,11 +462,7 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c
   const W n = c.n;
   const uint32_t pm = cfg.pmask, fl = cfg.flags;
   Pre<W> q;
-  q.lnT = m::log(T);
-  q.rT = m::rcp(T);
-  q.sqT = m::sqrt(T);
-  q.rsqT = m::rcp(q.sqT);
-  q.rTd = m::rcp(Td);
+  make_pre<W>(T, Td, q);
   const W rT = q.rT;
   Rates<W> r;
   eval_rates<W>(T, Td, q, c, cfg.rmask, r);

@@ -24,7 +24,7 @@ __device__ __forceinline__ int newton_species(double u[5], const double u0[5], d
   if (fr0 && fr1) return 0;
   Pre<double> q;
   const double T = u[2], Td = u[3];
-  q.lnT = log(T); q.rT = 1.0 / T; q.sqT = sqrt(T); q.rsqT = 1.0 / q.sqT; q.rTd = 1.0 / Td;
+  make_pre<double>(T, Td, q);
   Rates<double> r;
   eval_rates<double>(T, Td, q, k, cfg.rmask, r);
   const bool via_on = ((cfg.rmask >> 2) & 1u) && ((cfg.rmask >> 3) & 1u);
