@@ -88,7 +88,7 @@ def _grf_uniform(rng, n: int, sigma: float = 8.0) -> np.ndarray:
     kr = np.fft.rfftfreq(n)
     k2 = k[:, None, None] ** 2 + k[None, :, None] ** 2 + kr[None, None, :] ** 2
     filt = np.exp(-2.0 * (np.pi * sigma) ** 2 * k2)   # FT of a unit-sum Gaussian, periodic
-    g = np.fft.irfftn(np.fft.rfftn(w) * filt, s=(n, n, n))
+    g = np.fft.irfftn(np.fft.rfftn(w) * filt, s=(n, n, n), axes=(0, 1, 2))
     g = (g - g.mean()) / g.std()
     return ndtr(g)
 
@@ -99,7 +99,7 @@ def _grf_normal(rng, n: int, sigma: float = 8.0) -> np.ndarray:
     kr = np.fft.rfftfreq(n)
     k2 = k[:, None, None] ** 2 + k[None, :, None] ** 2 + kr[None, None, :] ** 2
     filt = np.exp(-2.0 * (np.pi * sigma) ** 2 * k2)
-    g = np.fft.irfftn(np.fft.rfftn(w) * filt, s=(n, n, n))
+    g = np.fft.irfftn(np.fft.rfftn(w) * filt, s=(n, n, n), axes=(0, 1, 2))
     return (g - g.mean()) / g.std()
 
 
