@@ -181,6 +181,12 @@ template <> __device__ __forceinline__ double pow2_neg<double>(int n) {
   return __longlong_as_double((long long)(1023 - n) << 52);
 }
 template <> __device__ __forceinline__ float pow2_neg<float>(int n) { return __int_as_float((127 - n) << 23); }
+// x 2^-n for a positive double whose exponent field exceeds n (a substep
+// length: at least the smallest FP32 subnormal, with n <= 30), by taking n
+// from the exponent field: exact, and integer instructions only.
+__device__ __forceinline__ double scale_pow2_neg(double x, int n) {
+  return __longlong_as_double(__double_as_longlong(x) - ((long long)n << 52));
+}
 
 // ----------------------------------------------------------- per-cell inputs
 // Quantities a cell keeps over one call, computed once in FP64 and held in
@@ -454,7 +460,7 @@ __device__ __forceinline__ W kappa_w(W T, W &beta_emit, W &beta_abs) {
 }
 
 template <typename W>
-__device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c, const DevCfg &cfg,
+__device__ __forceinline__ void eval_system(const double u[5], double yH64, const CellK<W> &c, const DevCfg &cfg,
                                             const CfgW<W> &cw, Sys<W> &S) {
   typedef M<W> m;
   const W y2 = to_w<W>(u[0]), ye = to_w<W>(u[1]), T = to_w<W>(u[2]), Td = to_w<W>(u[3]), E = to_w<W>(u[4]);
@@ -467,8 +473,9 @@ __device__ __forceinline__ void eval_system(const double u[5], const CellK<W> &c
   Rates<W> r;
   eval_rates<W>(T, Td, q, c, cfg.rmask, r);
   // differences that cancel are taken in FP64 and rounded once: y_H near 0
-  // (fully molecular or ionized gas) and T_d - T_g in tight gas-dust coupling
-  const W yH = to_w<W>(1.0 - 2.0 * u[0] - u[1]);
+  // (fully molecular or ionized gas; yH64 = 1 - 2 y_H2 - y_e, formed by the
+  // caller) and T_d - T_g in tight gas-dust coupling
+  const W yH = to_w<W>(yH64);
   const W dTdg = to_w<W>(u[3] - u[2]);
   S.dTdg = dTdg;
   const bool via_on = ((cfg.rmask >> 2) & 1u) && ((cfg.rmask >> 3) & 1u);

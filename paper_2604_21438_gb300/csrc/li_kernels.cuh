@@ -162,24 +162,26 @@ __device__ __forceinline__ W damp_factor(W Td, W E, W dTd, W dE) {
 // Tight coupling (Sec. 2.2.8): Newton iteration of the backward-Euler
 // residual of the dust row (Eq. ap_eq:dust_temp) and the IR row
 // (Eq. ap_eq:Eir) at the substep's new T_g and abundances.  The iterate is
-// the FP64 starting point plus corrections accumulated in W, so the loop
-// itself runs in W; the corrections are added to the FP64 state once at the
-// end.  Returns the iteration count, negative when nr_itr_limit was reached.
-// Inputs in W: T (= T_g, fixed), Tb / Eb (the starting point), g3 / g4 (the
-// starting point minus the substep's start), dTg (T_d - T_g at the
-// starting point) and dtw (the substep).  The FP64 path forms them exactly from the FP64 state; the
-// mixed path from its W-precision view of the state and the LI increments.
+// the starting point plus corrections accumulated in W, so the loop itself
+// runs in W; the corrections come back in a3 / a4 (T_d, E_IR) and the caller
+// adds them to its FP64 state once.  Returns the iteration count, negative
+// when nr_itr_limit was reached.  Inputs in W: T (= T_g, fixed), Tb / Eb
+// (the starting point), g3 / g4 (the starting point minus the substep's
+// start), dTg (T_d - T_g at the starting point) and dtw (the substep).  The
+// FP64 path forms them exactly from the FP64 state; the mixed path from its
+// W-precision view of the state and the LI increments.
 template <typename W>
-__device__ __forceinline__ int newton_dust_w(double u[5], W T, W Tb, W Eb, W g3, W g4, W dTg, W dtw,
+__device__ __forceinline__ int newton_dust_w(W &a3, W &a4, W T, W Tb, W Eb, W g3, W g4, W dTg, W dtw,
                                              const CellK<W> &c, const DevCfg &cfg, W tol) {
   typedef M<W> m;
   const bool frTd = cfg.flags & F_FTD, frE = cfg.flags & F_FE;
+  a3 = W(0);                                    // accumulated corrections
+  a4 = W(0);
   if (frTd && frE) return 0;
   const uint32_t pm = cfg.pmask;
   const W G = c.Gpre * m::sqrt(T);
   const W gam = W(1) - W(0.8) * m::exp(W(-TLOW) * m::rcp(T));
   const W rho = c.rho, fd = c.fd;
-  W a3 = W(0), a4 = W(0);                       // accumulated corrections
   int result = -cfg.nr_itr_limit;
   bool polish = false;
   for (int it = 1; it <= cfg.nr_itr_limit + 1; ++it) {
@@ -219,22 +221,19 @@ __device__ __forceinline__ int newton_dust_w(double u[5], W T, W Tb, W Eb, W g3,
     if (polish) { result = it - 1; break; }
     if (lam == W(1) && m::abs(d0) <= tol * (Tb + a3) && m::abs(d1) <= tol * (Eb + a4)) polish = true;
   }
-  u[3] += to_f64(a3);
-  u[4] += to_f64(a4);
-  if constexpr (sizeof(W) == sizeof(double)) {
-    u[3] = fmax(u[3], TCMB);
-    u[4] = fmax(u[4], EFLOOR);
-  } else {
-    u[3] = max_bits(u[3], TCMB);
-    u[4] = max_bits(u[4], EFLOOR);
-  }
   return result;
 }
 
-// FP64 entry: the starting point is the FP64 state u, the substep's start u0.
+// FP64 entry: the starting point is the FP64 state u, the substep's start u0;
+// the corrections are added to u.
 __device__ __forceinline__ int newton_dust(double u[5], const double u0[5], double dt, const CellK<double> &c,
                                            const DevCfg &cfg, double tol) {
-  return newton_dust_w<double>(u, u[2], u[3], u[4], u[3] - u0[3], u[4] - u0[4], u[3] - u[2], dt, c, cfg, tol);
+  double a3, a4;
+  const int it =
+      newton_dust_w<double>(a3, a4, u[2], u[3], u[4], u[3] - u0[3], u[4] - u0[4], u[3] - u[2], dt, c, cfg, tol);
+  u[3] = fmax(u[3] + a3, TCMB);
+  u[4] = fmax(u[4] + a4, EFLOOR);
+  return it;
 }
 
 // ------------------------------------------------------------- one cell
@@ -302,7 +301,21 @@ __device__ __forceinline__ float residual_ff(float b, const float *a, const floa
 template <typename W, bool MIXED>
 __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, const CfgW<W> &cw) {
   Sys<W> S;
-  eval_system<W>(c.u, c.k, cfg, cw, S);
+  double yH;
+  if constexpr (MIXED) {
+    // The projection's bound y_H2 <= (1 - y_e)/2 is applied here, at the
+    // next use of the state, where y_H = 1 - 2 y_H2 - y_e is formed anyway: a
+    // negative y_H (sign bit) is the violated bound.  The FP64 arithmetic of
+    // the bound then runs only in the lanes where it binds.
+    yH = fma(-2.0, c.u[0], 1.0) - c.u[1];
+    if (__double_as_longlong(yH) < 0) {
+      c.u[0] = (1.0 - c.u[1]) * 0.5;
+      yH = max_bits(fma(-2.0, c.u[0], 1.0) - c.u[1], 0.0);
+    }
+  } else {
+    yH = 1.0 - 2.0 * c.u[0] - c.u[1];
+  }
+  eval_system<W>(c.u, yH, c.k, cfg, cw, S);
   const double dt_h = c.k.dt_h;
   if (c.mode < 0) {
     // estimated subcycles dt_hydro / (f_chem dt_dust) against N_cyc, from the start state
@@ -333,7 +346,7 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
     dts = fits ? rem : dtc;
     dw = fits ? remw : dtcw;
     if (c.nri != 0) {
-      dts *= pow2_neg<double>(c.nri);
+      dts = scale_pow2_neg(dts, c.nri);
       dw *= pow2_neg<W>(c.nri);
     }
   } else {
@@ -414,25 +427,24 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
 #pragma unroll
   for (int i = 2; i < 5; ++i) x[i] += dx[i];
   c.u[2] = fma(c.u[2], to_f64(x[2]), c.u[2]);
-  c.u[3] = fma(c.u[3], to_f64(x[3]), c.u[3]);
-  c.u[4] = fma(c.u[4], to_f64(x[4]), c.u[4]);
+  // (the mixed path's tight-coupling lanes add the LI increments of T_d and
+  // E_IR together with the Newton corrections, below)
+  if (!MIXED || c.mode != 1) {
+    c.u[3] = fma(c.u[3], to_f64(x[3]), c.u[3]);
+    c.u[4] = fma(c.u[4], to_f64(x[4]), c.u[4]);
+  }
   if constexpr (MIXED) {
     // The projection of project() without the FP64 pipe where the bound is
-    // a constant (integer clamps on the bit patterns, the same values).  Only
-    // y_H2 <= (1 - y_e)/2 needs FP64 arithmetic; a W-precision estimate of the
-    // new state, with a margin far above its rounding error, decides whether
-    // it can bind.  (As one FP64 branch for all bounds, the projection ran in
-    // most warps for a few of their lanes, and an FP64 warp instruction
-    // occupies the pipe whatever its number of active lanes.)
+    // a constant (integer clamps on the bit patterns, the same values); the
+    // bound y_H2 <= (1 - y_e)/2 is applied where y_H is next formed (the
+    // next substep, or the store of the finished cell).  An FP64 warp
+    // instruction occupies the pipe whatever its number of active lanes, so
+    // FP64 code that a few lanes need is kept out of the common path.
     c.u[1] = min_bits(max_bits(c.u[1], 0.0), 1.0);
     c.u[0] = max_bits(c.u[0], 0.0);
     c.u[2] = max_bits(c.u[2], TCMB);
     c.u[3] = max_bits(c.u[3], TCMB);
     c.u[4] = max_bits(c.u[4], EFLOOR);
-    const W y2n = S.uf[0] + x[0] + dx[0], yen = S.uf[1] + x[1] + dx[1];
-    const W e2 = W(1e-4) * (m_abs(S.uf[0]) + m_abs(x[0]) + m_abs(dx[0]));
-    const W ee = W(1e-4) * (m_abs(S.uf[1]) + m_abs(x[1]) + m_abs(dx[1]));
-    if (!(y2n + e2 < (W(1) - yen - ee) * W(0.5) - W(1e-6))) c.u[0] = fmin(c.u[0], (1.0 - c.u[1]) * 0.5);
   } else {
     project(c.u);
   }
@@ -440,18 +452,17 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
     // the iteration starts from the LI update of (T_d, E_IR), limited like a Newton correction
     int it;
     if constexpr (MIXED) {
-      // W-precision view of the updated state: the start values plus the LI increments
-      W d3 = S.uf[3] * x[3], d4 = S.uf[4] * x[4];
-      const W lam = damp_factor<W>(S.uf[3], S.uf[4], d3, d4);
-      if (lam < W(1)) {
-        c.u[3] = fmax(u0[3] + to_f64(lam) * (c.u[3] - u0[3]), TCMB);
-        c.u[4] = fmax(u0[4] + to_f64(lam) * (c.u[4] - u0[4]), EFLOOR);
-        d3 = to_w<W>(c.u[3] - u0[3]);
-        d4 = to_w<W>(c.u[4] - u0[4]);
-      }
+      // W-precision view of the updated state: the start values plus the
+      // (limited) LI increments; the state takes the LI increment and the
+      // Newton corrections in one FP64 add each
+      const W lam = damp_factor<W>(S.uf[3], S.uf[4], S.uf[3] * x[3], S.uf[4] * x[4]);
+      const W d3 = lam * (S.uf[3] * x[3]), d4 = lam * (S.uf[4] * x[4]);
       const W d2 = S.uf[2] * x[2];
-      it = newton_dust_w<W>(c.u, S.uf[2] + d2, S.uf[3] + d3, S.uf[4] + d4, d3, d4, S.dTdg + (d3 - d2), dw, c.k,
-                            cfg, cw.nr_tol);
+      W a3, a4;
+      it = newton_dust_w<W>(a3, a4, S.uf[2] + d2, S.uf[3] + d3, S.uf[4] + d4, d3, d4, S.dTdg + (d3 - d2), dw,
+                            c.k, cfg, cw.nr_tol);
+      c.u[3] = max_bits(u0[3] + to_f64(d3 + a3), TCMB);
+      c.u[4] = max_bits(u0[4] + to_f64(d4 + a4), EFLOOR);
     } else {
       const double lam = damp_factor<double>(u0[3], u0[4], c.u[3] - u0[3], c.u[4] - u0[4]);
       if (lam < 1.0) {
@@ -607,6 +618,10 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
       if constexpr (NR) done = nr_attempt(c, cfg, cw);
       else done = li_substep<W, MIXED>(c, cfg, cw);
       if (done) {
+        if constexpr (MIXED && !NR) {
+          // the bound y_H2 <= (1 - y_e)/2 not yet applied to the last update
+          if (__double_as_longlong(fma(-2.0, c.u[0], 1.0) - c.u[1]) < 0) c.u[0] = (1.0 - c.u[1]) * 0.5;
+        }
         a.y2[idx] = c.u[0]; a.ye[idx] = c.u[1]; a.Tg[idx] = c.u[2]; a.Td[idx] = c.u[3]; a.E[idx] = c.u[4];
         if (a.yH) a.yH[idx] = 1.0 - 2.0 * c.u[0] - c.u[1];
         if (a.yHp) a.yHp[idx] = c.u[1];

@@ -58,7 +58,7 @@ __device__ __forceinline__ bool nr_inner(double Tg, const double u0[5], double d
   if (newton_dust(uo, u0, dt, k, cfg, tol) < 0) return false;
   if (newton_species(uo, u0, dt, k, cfg, tol) < 0) return false;
   Sys<double> S;
-  eval_system<double>(uo, k, cfg, cw, S);
+  eval_system<double>(uo, 1.0 - 2.0 * uo[0] - uo[1], k, cfg, cw, S);
   const double ytot0 = 1.0 - u0[0] + u0[1] + YHE;
   g = ytot0 * (Tg - u0[2]) / (cfg.gamma_ad - 1.0) - dt * S.H;
   return true;
