@@ -147,24 +147,26 @@ template <> struct M<float> {
 // nearest (ties away from zero); results below the FP32 normal range become
 // signed zeros, above it signed infinities; NaN stays NaN.
 __device__ __forceinline__ double f2d_int(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t sgn = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
-  const uint32_t e64 = (e == 0xffu) ? 0x7ffu : e + 896u;            // rebias 127 -> 1023
-  const uint32_t hi = (e == 0u) ? sgn : (sgn | (e64 << 20) | (m >> 3));
-  const uint32_t lo = (e == 0u) ? 0u : (m << 29);
+  const uint32_t u = __float_as_uint(f), a = u & 0x7fffffffu;
+  const bool tiny = a < 0x00800000u;                                // zero or subnormal
+  // exponent and mantissa shifted into place, the exponent rebiased 127 -> 1023
+  // (255 -> 2047 for inf and NaN)
+  uint32_t hi = (a >> 3) + (a >= 0x7f800000u ? 0x70000000u : 0x38000000u);
+  hi = (tiny ? 0u : hi) | (u & 0x80000000u);
+  const uint32_t lo = tiny ? 0u : (u << 29);
   return __hiloint2double((int)hi, (int)lo);
 }
 __device__ __forceinline__ float d2f_int(double d) {
   const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
-  const uint32_t sgn = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 896;                   // rebias 1023 -> 127
-  const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  uint32_t bits = (sgn | ((uint32_t)e << 23) | m) + ((lo >> 28) & 1u); // a carry rounds into the exponent
-  const bool special = ((hi >> 20) & 0x7ffu) == 0x7ffu;
-  const bool is_nan = special && (((hi & 0xfffffu) | lo) != 0u);
-  bits = (e <= 0) ? sgn : bits;
-  bits = (e >= 255 || special) ? (sgn | 0x7f800000u) : bits;
-  bits = is_nan ? 0x7fc00000u : bits;
+  const uint32_t a = hi & 0x7fffffffu;
+  // exponent and the top 23 mantissa bits, rebiased 1023 -> 127 modulo 2^32
+  // (exact inside the FP32 normal range), plus the rounding bit; a carry
+  // rounds into the exponent
+  uint32_t bits = ((a << 3) | (lo >> 29)) + 0x40000000u + ((lo >> 28) & 1u);
+  bits = (a < 0x38100000u) ? 0u : bits;                             // below the normal range
+  bits = (a >= 0x47f00000u) ? 0x7f800000u : bits;                   // above it (and inf, NaN)
+  bits |= hi & 0x80000000u;
+  bits = (a > 0x7ff00000u || (a == 0x7ff00000u && lo != 0u)) ? 0x7fc00000u : bits;
   return __uint_as_float(bits);
 }
 template <typename W> __device__ __forceinline__ W to_w(double d);

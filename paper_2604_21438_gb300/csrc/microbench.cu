@@ -1,6 +1,7 @@
 // microbench.cu -- FMA-throughput microbenchmarks used as measured ALU
-// denominators of the roofline (FP64 and FP32 vector pipes), and a device
-// check of the solver's FP32 math functions against CUDA's.  Each FMA thread
+// denominators of the roofline (FP64 and FP32 vector pipes), and device
+// checks of the solver's FP32 math functions and of its integer FP32 <-> FP64
+// conversions against CUDA's.  Each FMA thread
 // runs 8 independent chains in registers; one launch covers every SM several
 // times over.  Not part of the solver.
 #include <cuda_runtime.h>
@@ -85,6 +86,43 @@ extern "C" int sfbench_math_check(int fn, int n, const float *x, float *ours, fl
   }
   if (!rc && cudaMemcpy(ours, d + n, sizeof(float) * n, cudaMemcpyDeviceToHost) != cudaSuccess) rc = 1;
   if (!rc && cudaMemcpy(ref, d + 2 * (size_t)n, sizeof(float) * n, cudaMemcpyDeviceToHost) != cudaSuccess) rc = 1;
+  cudaFree(d);
+  return rc;
+}
+
+// The mixed path's integer conversions against the hardware ones: f2d_ours[i]
+// = f2d_int(xf[i]), f2d_ref[i] = (double)xf[i]; d2f_ours[i] = d2f_int(xd[i]),
+// d2f_ref[i] = __double2float_rn(xd[i]).  Host buffers of n elements each.
+__global__ void conv_check(int n, const float *xf, double *f2d_ours, double *f2d_ref, const double *xd,
+                           float *d2f_ours, float *d2f_ref) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  f2d_ours[i] = sfc::f2d_int(xf[i]);
+  f2d_ref[i] = (double)xf[i];
+  d2f_ours[i] = sfc::d2f_int(xd[i]);
+  d2f_ref[i] = __double2float_rn(xd[i]);
+}
+
+extern "C" int sfbench_conv_check(int n, const float *xf, double *f2d_ours, double *f2d_ref, const double *xd,
+                                  float *d2f_ours, float *d2f_ref) {
+  if (n <= 0 || !xf || !f2d_ours || !f2d_ref || !xd || !d2f_ours || !d2f_ref) return 1;
+  const size_t N = (size_t)n;
+  char *d = nullptr;
+  const size_t bytes = N * (sizeof(float) * 3 + sizeof(double) * 3);
+  if (cudaMalloc(&d, bytes) != cudaSuccess) return 1;
+  double *dxd = (double *)d, *dfo = dxd + N, *dfr = dfo + N;
+  float *dxf = (float *)(dfr + N), *ddo = dxf + N, *ddr = ddo + N;
+  int rc = 0;
+  if (cudaMemcpy(dxf, xf, sizeof(float) * N, cudaMemcpyHostToDevice) != cudaSuccess) rc = 1;
+  if (!rc && cudaMemcpy(dxd, xd, sizeof(double) * N, cudaMemcpyHostToDevice) != cudaSuccess) rc = 1;
+  if (!rc) {
+    conv_check<<<(n + 255) / 256, 256>>>(n, dxf, dfo, dfr, dxd, ddo, ddr);
+    if (cudaGetLastError() != cudaSuccess) rc = 1;
+  }
+  if (!rc && cudaMemcpy(f2d_ours, dfo, sizeof(double) * N, cudaMemcpyDeviceToHost) != cudaSuccess) rc = 1;
+  if (!rc && cudaMemcpy(f2d_ref, dfr, sizeof(double) * N, cudaMemcpyDeviceToHost) != cudaSuccess) rc = 1;
+  if (!rc && cudaMemcpy(d2f_ours, ddo, sizeof(float) * N, cudaMemcpyDeviceToHost) != cudaSuccess) rc = 1;
+  if (!rc && cudaMemcpy(d2f_ref, ddr, sizeof(float) * N, cudaMemcpyDeviceToHost) != cudaSuccess) rc = 1;
   cudaFree(d);
   return rc;
 }

@@ -49,3 +49,45 @@ def test_rcp_and_sqrt():
     assert _ulp(ours, ref).max() <= 1.0
     ours, ref = _check(3, np.abs(x))
     assert _ulp(ours, ref).max() <= 1.0
+
+
+def test_integer_conversions_match_the_hardware():
+    """f2d_int / d2f_int (the mixed path's FP32 <-> FP64 conversions on the
+    integer pipe) against CUDA's conversions: bitwise equal on normal numbers,
+    zeros, infinities and NaN; d2f rounds ties away from zero where CUDA
+    rounds them to even; FP32 subnormals, in and out, become signed zeros."""
+    from paper_2604_21438_gb300 import _build
+    _build.build()
+    L = ctypes.CDLL(_build.BENCH_LIB)
+    f32 = np.finfo(np.float32)
+    n = 1 << 20
+    xf = (10.0 ** RNG.uniform(-37.9, 38.5, n) * RNG.choice([-1.0, 1.0], n)).astype(np.float32)
+    xf[:8] = [0.0, -0.0, np.inf, -np.inf, np.nan, f32.tiny, -f32.max, 1e-40]
+    xd = 10.0 ** RNG.uniform(-37.9, 38.5, n) * RNG.choice([-1.0, 1.0], n)
+    # exact ties of the FP32 rounding: a float plus half of its last place
+    t = (10.0 ** RNG.uniform(-30.0, 30.0, 1000)).astype(np.float32).astype(np.float64)
+    xd[8:1008] = t + 0.5 * np.spacing(t.astype(np.float32)).astype(np.float64)
+    xd[:8] = [0.0, -0.0, np.inf, -np.inf, np.nan, 3.5e38, 1e-39, float(f32.max) * (1 + 2.0 ** -25)]
+    fo, fr, do_, dr = np.empty(n), np.empty(n), np.empty(n, np.float32), np.empty(n, np.float32)
+    p = lambda a: ctypes.c_void_p(a.ctypes.data)
+    assert L.sfbench_conv_check(n, p(xf), p(fo), p(fr), p(xd), p(do_), p(dr)) == 0
+    # f2d
+    sub = (xf != 0) & (np.abs(xf) < f32.tiny)
+    assert np.all(fo[sub] == 0.0) and np.all(np.signbit(fo[sub]) == np.signbit(xf[sub]))
+    ok = ~sub & ~np.isnan(xf)
+    assert np.array_equal(fo[ok].view(np.uint64), fr[ok].view(np.uint64))
+    assert np.all(np.isnan(fo[np.isnan(xf)]))
+    # d2f
+    tie = np.zeros(n, bool)
+    tie[8:1008] = True
+    small = np.isfinite(xd) & (np.abs(xd) < f32.tiny)
+    assert np.all(do_[small] == 0.0)
+    rest = ~tie & ~small
+    a, b = do_[rest], dr[rest]
+    both_nan = np.isnan(a) & np.isnan(b)
+    assert np.array_equal(a[~both_nan].view(np.uint32), b[~both_nan].view(np.uint32))
+    assert np.all(np.isnan(a) == np.isnan(b))
+    # ties: away from zero, one place from CUDA's where that rounds to even
+    ta = do_[tie].astype(np.float64)
+    assert np.all(np.abs(ta) > np.abs(xd[tie]))
+    assert np.all(np.abs(ta - dr[tie].astype(np.float64)) <= np.spacing(np.abs(dr[tie])).astype(np.float64))
