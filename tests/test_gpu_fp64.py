@@ -151,3 +151,29 @@ def test_batched_amr_blocks_match_oracle():
     ref = oracle.li_step(inputs.subset(cells, idx), bdt[blk], 100.0)
     cell_dt = bdt[np.searchsorted(off, np.arange(len(cells["n_H"])), side="right") - 1]
     assert_parity(got, ref, idx=idx, cells=cells, dt=cell_dt, cd=100.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_call_statistics_match_the_cells_and_the_oracle(precision):
+    """sfchem_stats of one call: totals equal to the sums over the cells'
+    own n_sub and status outputs (the per-warp reduction drops nothing), and,
+    for the FP64 path, to the oracle's counts: substeps, Newton iterations of
+    the tight-coupling mode, tight / capped cells (on these cells every
+    substep count and status bit of the FP64 path equals the oracle's)."""
+    cells = inputs.cells_uniform(4096, seed=1001)
+    dt = 1e3 * YR
+    got = run_gpu(cells, dt, 1.0, precision=precision)
+    st = got["_stats"]
+    ns, status = got["n_sub"].astype(np.int64), got["status"].astype(np.int64)
+    assert st["calls"] == 1 and st["cells"] == 4096
+    assert st["substeps"] == ns.sum() and st["max_substeps"] == ns.max()
+    assert st["tight_cells"] == int(((status & 8) != 0).sum())
+    assert st["capped_cells"] == int(((status & 1) != 0).sum())
+    assert st["noconv_cells"] == int(((status & 4) != 0).sum())
+    assert st["badinput_cells"] == 0 and st["badstep_cells"] == int(((status & 16) != 0).sum())
+    if precision == "fp64":
+        ref = oracle.li_step(cells, dt, 1.0)
+        assert np.array_equal(got["n_sub"], ref["n_sub"]) and np.array_equal(got["status"], ref["status"])
+        assert st["newton_iters"] == int(ref["n_itr"].astype(np.int64).sum())
+    else:
+        assert st["tight_cells"] > 0 and st["newton_iters"] > 0
