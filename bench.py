@@ -39,12 +39,12 @@ YR = inputs.YR
 # divided by the substeps of that launch (GRF 128^3 workload, dt = 1e3 yr,
 # C_d = 1e4); profiles/sfchem_li_{mixed,fp64}_grf128.md.
 WORK_PER_SUBSTEP = {
-    "mixed": {"fp32_flops": 1305.5, "fp64_flops": 48.0},
+    "mixed": {"fp32_flops": 1291.5, "fp64_flops": 48.0},
     "fp64": {"fp32_flops": 7.5, "fp64_flops": 2003.8},
 }
-# DRAM bytes per cell of one solver launch (same captures: 274.2 MB for
+# DRAM bytes per cell of one solver launch (same captures: 269.3 MB for
 # 2,097,152 cells, mixed; 274.6 MB, FP64).
-DRAM_BYTES_PER_CELL = {"mixed": 274.21e6 / 2097152, "fp64": 274.61e6 / 2097152}
+DRAM_BYTES_PER_CELL = {"mixed": 269.35e6 / 2097152, "fp64": 274.61e6 / 2097152}
 # GB300 ALU peaks from unit counts and the SM clock: 152 SMs; FP32 128
 # lanes/SM (256 flops/clk); FP64 2 DFMA/clk/SM (4 flops/clk) -- the
 # "peak_sustained" of the FP64 pipe that ncu reports, 1.26 TFLOP/s at 2.07 GHz.

@@ -63,6 +63,7 @@ constexpr uint32_t P_L13 = 1u << 12, P_GG = 1u << 13, P_UV = 1u << 14, P_EMIT = 
                    P_IRABS = 1u << 16;
 constexpr uint32_t F_FTG = 1u << 0, F_FTD = 1u << 1, F_FE = 1u << 2, F_FY2 = 1u << 3,
                    F_FYE = 1u << 4, F_SPLIT = 1u << 5, F_REFINE_FF = 1u << 6;
+constexpr uint32_t R_ALL = (1u << 12) - 1u, P_ALL = (1u << 17) - 1u;   // every reaction / process
 constexpr uint8_t ST_CAP = 1, ST_BAD = 2, ST_NOCONV = 4, ST_TIGHT = 8, ST_BADSTEP = 16;
 
 // Solver parameters as the kernels see them.
