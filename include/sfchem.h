@@ -237,7 +237,7 @@ int sfchem_step_batched(sfchem_ctx *ctx, const sfchem_state_t *state,
  * queued on `stream`, and the call returns when every result is in host
  * memory (it synchronizes `stream`).  Errors as sfchem_step_batched;
  * slice_cells < 0 is SFCHEM_EINVAL. */
-#define SFCHEM_HOST_SLICE_DEFAULT 4194304
+#define SFCHEM_HOST_SLICE_DEFAULT 16777216
 int sfchem_step_host(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_fields_t *fields,
                      const int64_t *block_offset, const double *block_dt, int32_t n_blocks,
                      double cd_factor, int64_t slice_cells, void *stream);
