@@ -64,3 +64,37 @@ def test_strerror_and_version():
         assert L.sfchem_strerror(code)
     assert L.sfchem_strerror(99) == b"unknown status"
     assert re.match(rb"\d+\.\d+\.\d+", L.sfchem_version())
+
+
+def _header_constants():
+    """Integer constants of the header's enums and #defines (1u << k and
+    (1u << k) - 1u forms), by name."""
+    txt = re.sub(r"/\*.*?\*/", "", open(HDR).read(), flags=re.S)
+    out = {}
+    for name, expr in re.findall(r"\b(SFCHEM_[A-Z0-9_]+)\s*=\s*([^,}\n]+)", txt):
+        expr = expr.strip()
+        m = re.fullmatch(r"\(1u << (\d+)\) - 1u", expr)
+        if m:
+            out[name] = (1 << int(m.group(1))) - 1
+            continue
+        m = re.fullmatch(r"1u << (\d+)", expr)
+        out[name] = (1 << int(m.group(1))) if m else int(expr)
+    for name, val in re.findall(r"#define\s+(SFCHEM_[A-Z0-9_]+)\s+(\d+)", txt):
+        out[name] = int(val)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    h = _header_constants()
+    assert (h["SFCHEM_FP64"], h["SFCHEM_MIXED"]) == (sf.FP64, sf.MIXED)
+    for k in ("OK", "EINVAL", "ENOTINIT", "ECUDA", "ETIMEOUT", "ENOMEM"):
+        assert h["SFCHEM_" + k] == getattr(sf, k), k
+    for k in ("CAP", "BADINPUT", "NOCONV", "TIGHT", "BADSTEP"):
+        assert h["SFCHEM_CELL_" + k] == getattr(sf, "CELL_" + k), k
+    for k in ("FREEZE_TG", "FREEZE_TD", "FREEZE_EIR", "FREEZE_YH2", "FREEZE_YE", "SPLIT", "REFINE_FF"):
+        assert h["SFCHEM_F_" + k] == getattr(sf, "F_" + k), k
+    assert h["SFCHEM_P_ALL"] == sf.P_ALL
+    assert h["SFCHEM_HOST_SLICE_DEFAULT"] > 0
+    # the process bits are the 17 distinct bits under P_ALL
+    bits = [v for k, v in h.items() if k.startswith("SFCHEM_P_") and k != "SFCHEM_P_ALL"]
+    assert len(bits) == 17 and sum(bits) == sf.P_ALL
