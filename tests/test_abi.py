@@ -98,3 +98,36 @@ def test_binding_constants_match_the_header():
     # the process bits are the 17 distinct bits under P_ALL
     bits = [v for k, v in h.items() if k.startswith("SFCHEM_P_") and k != "SFCHEM_P_ALL"]
     assert len(bits) == 17 and sum(bits) == sf.P_ALL
+
+
+def _device_constants():
+    """constexpr integer constants of the kernels' header (csrc/li_device.cuh)."""
+    path = os.path.join(os.path.dirname(HDR), "..", "paper_2604_21438_gb300", "csrc", "li_device.cuh")
+    txt = re.sub(r"//.*", "", open(path).read())
+    out = {}
+    for decl in re.findall(r"constexpr\s+uint(?:8|32)_t\s+([^;]+);", txt):
+        for name, expr in re.findall(r"([A-Z][A-Z0-9_]*)\s*=\s*([^,]+)", decl):
+            expr = expr.strip()
+            m = re.fullmatch(r"\(1u << (\d+)\) - 1u", expr)
+            if m:
+                out[name] = (1 << int(m.group(1))) - 1
+                continue
+            m = re.fullmatch(r"1u << (\d+)", expr)
+            out[name] = (1 << int(m.group(1))) if m else int(expr)
+    return out
+
+
+def test_kernel_constants_match_the_header():
+    """The kernels keep their own copies of the status, flag and mask bits;
+    they must equal the public header's."""
+    h, d = _header_constants(), _device_constants()
+    pairs = dict(ST_CAP="CELL_CAP", ST_BAD="CELL_BADINPUT", ST_NOCONV="CELL_NOCONV", ST_TIGHT="CELL_TIGHT",
+                 ST_BADSTEP="CELL_BADSTEP", F_FTG="F_FREEZE_TG", F_FTD="F_FREEZE_TD", F_FE="F_FREEZE_EIR",
+                 F_FY2="F_FREEZE_YH2", F_FYE="F_FREEZE_YE", F_SPLIT="F_SPLIT", F_REFINE_FF="F_REFINE_FF",
+                 P_ALL="P_ALL")
+    for dev, pub in pairs.items():
+        assert d[dev] == h["SFCHEM_" + pub], dev
+    dev_p = sorted(v for k, v in d.items() if k.startswith("P_") and k != "P_ALL")
+    pub_p = sorted(v for k, v in h.items() if k.startswith("SFCHEM_P_") and k != "SFCHEM_P_ALL")
+    assert dev_p == pub_p
+    assert d["R_ALL"] == (1 << 12) - 1        # reactions H0 ... H11 of Table 3
