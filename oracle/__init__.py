@@ -26,8 +26,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sfchem_oracle.cpp")
 _HDR = os.path.join(_HERE, "sfchem_oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
-_lock = threading.Lock()
+# A second build of the same source with floating-point contraction allowed
+# (-ffp-contract=fast): on a machine with fused multiply-add (aarch64) it is
+# the oracle with another, equally valid FP64 rounding sequence.  The tests
+# use it to measure how much a cell's result depends on FP64 rounding at all.
+_LIB_FMA = os.path.join(_HERE, "liboracle_fma.so")
+_lock = threading.RLock()
 _lib = None
+_lib_fma = None
 
 # process_mask bits (Table 4 rows and the Appendix C dust terms)
 P_G1_H2FORM, P_G2_PHOTOION, P_G3_PHOTODISS, P_G4_PHOTOELEC = 1 << 0, 1 << 1, 1 << 2, 1 << 3
@@ -38,6 +44,7 @@ P_ALL = (1 << 17) - 1
 P_GAS_ONLY = P_ALL & ~(P_GASGRAIN | P_DUST_UV | P_DUST_EMIT | P_DUST_IRABS)
 # flags
 F_FREEZE_TG, F_FREEZE_TD, F_FREEZE_EIR, F_FREEZE_YH2, F_FREEZE_YE, F_SPLIT = 1, 2, 4, 8, 16, 32
+F_NO_REJECT = 64   # paper-literal controller (no step rejection)
 F_FREEZE_THERMAL = F_FREEZE_TG | F_FREEZE_TD | F_FREEZE_EIR
 # status bits
 ST_CAP, ST_BADINPUT, ST_NOCONV, ST_TIGHT, ST_BADSTEP = 1, 2, 4, 8, 16
@@ -59,41 +66,114 @@ class OracleConfig(ctypes.Structure):
     ]
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so (plain g++, OpenMP) if missing or stale."""
+def build(force: bool = False, fma: bool = False) -> str:
+    """Compile liboracle.so (plain g++, OpenMP) if missing or stale
+    (fma=True: liboracle_fma.so, the same source with contraction allowed)."""
+    out = _LIB_FMA if fma else _LIB
     with _lock:
-        stale = (not os.path.exists(_LIB)) or any(
-            os.path.getmtime(p) > os.path.getmtime(_LIB) for p in (_SRC, _HDR))
+        stale = (not os.path.exists(out)) or any(
+            os.path.getmtime(p) > os.path.getmtime(out) for p in (_SRC, _HDR))
         if force or stale:
-            cmd = ["g++", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c++17",
-                   "-o", _LIB + ".tmp", _SRC]
+            # -ffp-contract=off: no fused multiply-adds the source does not ask
+            # for, so the oracle gives the same numbers on x86-64 and aarch64
+            contract = "-ffp-contract=fast" if fma else "-ffp-contract=off"
+            cmd = ["g++", "-O3", contract, "-fopenmp", "-fPIC", "-shared", "-std=c++17",
+                   "-o", out + ".tmp", _SRC]
             subprocess.run(cmd, check=True, cwd=_HERE)
-            os.replace(_LIB + ".tmp", _LIB)
-    return _LIB
+            os.replace(out + ".tmp", out)
+    return out
 
 
-def lib():
-    global _lib
+_OPC_SRC = os.path.join(_HERE, "opcount.cpp")
+_OPC_LIB = os.path.join(_HERE, "liboracle_opcount.so")
+_opc = None
+OPCOUNT_SECTIONS = ("system", "solve", "newton", "control")
+OPCOUNT_OPS = ("add", "mul", "div", "fma", "sqrt", "exp", "log", "pow", "cmp")
+
+
+def build_opcount(force: bool = False) -> str:
+    """Compile the op-counting build of the oracle (opcount.cpp) if stale."""
+    with _lock:
+        srcs = (_OPC_SRC, _SRC, _HDR)
+        stale = (not os.path.exists(_OPC_LIB)) or any(os.path.getmtime(p) > os.path.getmtime(_OPC_LIB) for p in srcs)
+        if force or stale:
+            cmd = ["g++", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c++17", "-o", _OPC_LIB + ".tmp",
+                   _OPC_SRC]
+            subprocess.run(cmd, check=True, cwd=_HERE)
+            os.replace(_OPC_LIB + ".tmp", _OPC_LIB)
+    return _OPC_LIB
+
+
+def opcount(cells: dict, dt, cd_factor: float = 1.0, cfg: OracleConfig | None = None) -> dict:
+    """Floating-point operations of the oracle's LI step on these cells,
+    counted by type and section (single thread).  Returns {"substeps": N,
+    "counts": {section: {op: count}}, "per_substep": {...}} where flops count
+    add/sub, mul and div as 1 and fma as 2, and sqrt / exp / log / pow are
+    reported apart."""
+    global _opc
+    if _opc is None:
+        build_opcount()
+        L = ctypes.CDLL(_OPC_LIB)
+        L.oracle_opcount_li.restype = ctypes.c_int64
+        _opc = L
+    cfg = cfg or default_config()
+    n = len(cells["n_H"])
+    a = {k: np.ascontiguousarray(cells[k], dtype=np.float64) for k in FIELDS_IN + FIELDS_STATE}
+    dtv = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
+    counts = np.zeros((len(OPCOUNT_SECTIONS), len(OPCOUNT_OPS)), np.uint64)
+    nsub = _opc.oracle_opcount_li(
+        ctypes.c_int64(n), _p(a["n_H"]), _p(a["T_g"]), _p(a["T_d"]), _p(a["E_IR"]), _p(a["y_H2"]), _p(a["y_e"]),
+        _p(a["G0"]), _p(a["n_EUV"]), _p(a["N_H2"]), _p(dtv), ctypes.c_double(cd_factor), ctypes.byref(cfg),
+        _p(counts))
+    if nsub < 0:
+        raise ValueError("oracle_opcount_li rejected its arguments")
+    out = {"substeps": int(nsub), "counts": {}, "per_substep": {}}
+    tot = np.zeros(len(OPCOUNT_OPS))
+    for i, sec in enumerate(OPCOUNT_SECTIONS):
+        out["counts"][sec] = {op: int(counts[i, j]) for j, op in enumerate(OPCOUNT_OPS)}
+        tot += counts[i]
+    per = tot / max(nsub, 1)
+    d = dict(zip(OPCOUNT_OPS, per))
+    out["per_substep"] = {op: float(v) for op, v in d.items()}
+    out["per_substep"]["flops"] = float(d["add"] + d["mul"] + d["div"] + 2 * d["fma"])
+    out["per_substep"]["transcendentals"] = float(d["sqrt"] + d["exp"] + d["log"] + d["pow"])
+    return out
+
+
+def lib(fma: bool = False):
+    global _lib, _lib_fma
+    if fma:
+        if _lib_fma is None:
+            build(fma=True)
+            _lib_fma = _setup(ctypes.CDLL(_LIB_FMA))
+        return _lib_fma
     if _lib is None:
         build()
-        L = ctypes.CDLL(_LIB)
-        dp = ctypes.POINTER(ctypes.c_double)
-        L.oracle_default_config.argtypes = [ctypes.POINTER(OracleConfig)]
-        L.oracle_li_cells.restype = ctypes.c_int
-        L.oracle_nr_cells.restype = ctypes.c_int
-        L.oracle_li_trace.restype = ctypes.c_int
-        L.oracle_li_trace.argtypes = [ctypes.c_double] * 11 + [
-            ctypes.POINTER(OracleConfig), ctypes.c_int, dp, ctypes.POINTER(ctypes.c_uint8)]
-        L.oracle_rates.argtypes = [ctypes.c_double] * 6 + [ctypes.POINTER(OracleConfig), dp]
-        L.oracle_system.argtypes = [ctypes.c_double, dp, ctypes.c_double, ctypes.c_double,
-                                    ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                    ctypes.POINTER(OracleConfig), dp, dp, dp, dp, dp, dp]
-        L.oracle_rhs.argtypes = [ctypes.c_double, dp, ctypes.c_double, ctypes.c_double,
-                                 ctypes.c_double, ctypes.c_double, ctypes.POINTER(OracleConfig), dp]
-        L.oracle_solve5.argtypes = [dp, dp, dp]
-        L.oracle_solve5.restype = ctypes.c_int
-        _lib = L
+        _lib = _setup(ctypes.CDLL(_LIB))
     return _lib
+
+
+def _setup(L):
+    """Argument and result types of the oracle's C functions."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.oracle_default_config.argtypes = [ctypes.POINTER(OracleConfig)]
+    L.oracle_li_cells.restype = ctypes.c_int
+    L.oracle_nr_cells.restype = ctypes.c_int
+    L.oracle_li_trace.restype = ctypes.c_int
+    L.oracle_li_trace.argtypes = [ctypes.c_double] * 11 + [
+        ctypes.POINTER(OracleConfig), ctypes.c_int, dp, ctypes.POINTER(ctypes.c_uint8)]
+    L.oracle_rates.argtypes = [ctypes.c_double] * 6 + [ctypes.POINTER(OracleConfig), dp]
+    L.oracle_system.argtypes = [ctypes.c_double, dp, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.POINTER(OracleConfig), dp, dp, dp, dp, dp, dp]
+    L.oracle_rhs.argtypes = [ctypes.c_double, dp, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_double, ctypes.c_double, ctypes.POINTER(OracleConfig), dp]
+    L.oracle_photon_update.restype = ctypes.c_int
+    L.oracle_set_perturbation.argtypes = [ctypes.c_double]
+    L.oracle_set_perturbation.restype = None
+    L.oracle_solve5.argtypes = [dp, dp, dp]
+    L.oracle_solve5.restype = ctypes.c_int
+    return L
 
 
 def default_config(**kw) -> OracleConfig:
@@ -113,10 +193,25 @@ FIELDS_STATE = ("T_g", "T_d", "E_IR", "y_H2", "y_e")
 
 
 def li_step(cells: dict, dt, cd_factor: float = 1.0, cfg: OracleConfig | None = None,
-            n_threads: int = 0) -> dict:
+            n_threads: int = 0, fma: bool = False, perturb: float = 0.0) -> dict:
     """LI step (Sec. 2.2.8) on a dict of 1-D float64 arrays; returns a new dict.
 
-    ``dt`` is a scalar (seconds) or one value per cell."""
+    ``dt`` is a scalar (seconds) or one value per cell; fma=True runs the
+    build with floating-point contraction allowed; perturb != 0 multiplies
+    every entry of each substep's linear system by 1 +- perturb (a test of
+    the result's sensitivity to rounding-level changes)."""
+    if perturb:
+        with _lock:
+            L = lib(fma)
+            L.oracle_set_perturbation(ctypes.c_double(perturb))
+            try:
+                return _li_step(cells, dt, cd_factor, cfg, n_threads, fma)
+            finally:
+                L.oracle_set_perturbation(ctypes.c_double(0.0))
+    return _li_step(cells, dt, cd_factor, cfg, n_threads, fma)
+
+
+def _li_step(cells, dt, cd_factor, cfg, n_threads, fma):
     cfg = cfg or default_config()
     n = len(cells["n_H"])
     st = {k: np.array(cells[k], dtype=np.float64, copy=True) for k in FIELDS_STATE}
@@ -126,16 +221,36 @@ def li_step(cells: dict, dt, cd_factor: float = 1.0, cfg: OracleConfig | None = 
     status = np.zeros(n, np.uint8)
     n_sub = np.zeros(n, np.int32)
     n_itr = np.zeros(n, np.int32)
-    rc = lib().oracle_li_cells(
+    n_rej = np.zeros((n, 2), np.int32)
+    rc = lib(fma).oracle_li_cells(
         ctypes.c_int64(n), _p(ins["n_H"]), _p(st["T_g"]), _p(st["T_d"]), _p(st["E_IR"]),
         _p(st["y_H2"]), _p(st["y_e"]), _p(out["y_H"]), _p(out["y_Hp"]), _p(out["y_Hm"]),
-        _p(status), _p(n_sub), _p(n_itr), _p(ins["G0"]), _p(ins["n_EUV"]), _p(ins["N_H2"]),
+        _p(status), _p(n_sub), _p(n_itr), _p(n_rej), _p(ins["G0"]), _p(ins["n_EUV"]), _p(ins["N_H2"]),
         _p(dtv), ctypes.c_double(cd_factor), ctypes.byref(cfg), ctypes.c_int(n_threads))
     if rc != 0:
         raise ValueError("oracle_li_cells rejected its arguments")
     st.update(out)
-    st.update(status=status, n_sub=n_sub, n_itr=n_itr)
+    st.update(status=status, n_sub=n_sub, n_itr=n_itr, n_rej=n_rej[:, 0].copy(), n_halv=n_rej[:, 1].copy())
     return st
+
+
+HNU_FUV = 12.4 * 1.602176634e-12    # erg: mean FUV photon energy (stand-in)
+U_HABING = 5.29e-14                 # erg cm^-3 per Habing unit (stand-in)
+
+
+def photon_update(cells: dict, dt) -> dict:
+    """Photon consumption after the update (oracle_photon_update): returns
+    {"G0", "n_EUV", "absorbed"} with absorbed[:, 0..3] = EUV by H, EUV by
+    dust, FUV by H2, FUV by dust (photons cm^-3)."""
+    n = len(cells["n_H"])
+    a = {k: np.ascontiguousarray(cells[k], dtype=np.float64) for k in ("n_H", "y_H2", "y_e", "G0", "n_EUV", "N_H2")}
+    dtv = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
+    G0, nE, ab = np.empty(n), np.empty(n), np.empty((n, 4))
+    rc = lib().oracle_photon_update(ctypes.c_int64(n), _p(a["n_H"]), _p(a["y_H2"]), _p(a["y_e"]), _p(a["G0"]),
+                                    _p(a["n_EUV"]), _p(a["N_H2"]), _p(dtv), _p(G0), _p(nE), _p(ab))
+    if rc != 0:
+        raise ValueError("oracle_photon_update rejected its arguments")
+    return {"G0": G0, "n_EUV": nE, "absorbed": ab}
 
 
 def nr_step(cells: dict, dt, cd_factor: float = 1.0, cfg: OracleConfig | None = None,

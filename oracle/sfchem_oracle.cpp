@@ -32,6 +32,19 @@
 
 namespace {
 
+// The arithmetic type of the LI step and the NR reference.  It is double in
+// every build the tests and the benchmark load; the op-counting build
+// (opcount.cpp) compiles this file with a counting scalar type in its place,
+// to count the method's floating-point work per substep.
+#ifdef SFCHEM_ORACLE_REAL
+typedef SFCHEM_ORACLE_REAL real;
+#else
+typedef double real;
+#endif
+#ifndef ORACLE_SECTION
+#define ORACLE_SECTION(k)
+#endif
+
 // ---------------------------------------------------------------- constants
 const double kB = 1.380649e-16;        // erg/K
 const double mH = 1.67262192e-24;      // g, mass of the hydrogen nucleus (App. C)
@@ -62,34 +75,35 @@ const double kap0 = 0.1, kap_T0 = 10.0, kap_Tc = 200.0; // kappa_d^0(T) = kap0 (
 const double sigma_dUV = 1.0e-21;   // cm^2 per H, dust UV cross-section
 const double u_Habing = 5.29e-14;   // erg cm^-3 per G0
 const double hnu_EUV = 18.0 * eV;   // mean EUV photon energy
+const double hnu_FUV = 12.4 * eV;   // mean FUV (Lyman-Werner band) photon energy
 
 // --------------------------------------------------------------- dual numbers
 // Forward-mode dual number over the four variables the chemistry and the gas
 // heating/cooling depend on: (y_H2, y_e, T_g, T_d).
 const int NV = 4;
 struct Dual {
-  double v;
-  double g[NV];
+  real v;
+  real g[NV];
 };
-Dual cst(double v) { Dual r; r.v = v; for (int i = 0; i < NV; ++i) r.g[i] = 0.0; return r; }
-Dual var(double v, int k) { Dual r = cst(v); r.g[k] = 1.0; return r; }
+Dual cst(real v) { Dual r; r.v = v; for (int i = 0; i < NV; ++i) r.g[i] = 0.0; return r; }
+Dual var(real v, int k) { Dual r = cst(v); r.g[k] = 1.0; return r; }
 Dual operator+(const Dual &a, const Dual &b) { Dual r; r.v = a.v + b.v; for (int i = 0; i < NV; ++i) r.g[i] = a.g[i] + b.g[i]; return r; }
 Dual operator-(const Dual &a, const Dual &b) { Dual r; r.v = a.v - b.v; for (int i = 0; i < NV; ++i) r.g[i] = a.g[i] - b.g[i]; return r; }
 Dual operator*(const Dual &a, const Dual &b) { Dual r; r.v = a.v * b.v; for (int i = 0; i < NV; ++i) r.g[i] = a.g[i] * b.v + a.v * b.g[i]; return r; }
 Dual operator/(const Dual &a, const Dual &b) { Dual r; r.v = a.v / b.v; for (int i = 0; i < NV; ++i) r.g[i] = (a.g[i] * b.v - a.v * b.g[i]) / (b.v * b.v); return r; }
-Dual operator+(const Dual &a, double s) { Dual r = a; r.v += s; return r; }
-Dual operator+(double s, const Dual &a) { return a + s; }
-Dual operator-(const Dual &a, double s) { Dual r = a; r.v -= s; return r; }
-Dual operator-(double s, const Dual &a) { Dual r; r.v = s - a.v; for (int i = 0; i < NV; ++i) r.g[i] = -a.g[i]; return r; }
+Dual operator+(const Dual &a, real s) { Dual r = a; r.v += s; return r; }
+Dual operator+(real s, const Dual &a) { return a + s; }
+Dual operator-(const Dual &a, real s) { Dual r = a; r.v -= s; return r; }
+Dual operator-(real s, const Dual &a) { Dual r; r.v = s - a.v; for (int i = 0; i < NV; ++i) r.g[i] = -a.g[i]; return r; }
 Dual operator-(const Dual &a) { return 0.0 - a; }
-Dual operator*(const Dual &a, double s) { Dual r; r.v = a.v * s; for (int i = 0; i < NV; ++i) r.g[i] = a.g[i] * s; return r; }
-Dual operator*(double s, const Dual &a) { return a * s; }
-Dual operator/(const Dual &a, double s) { return a * (1.0 / s); }
-Dual operator/(double s, const Dual &a) { return cst(s) / a; }
-Dual dexp(const Dual &a) { double e = std::exp(a.v); Dual r; r.v = e; for (int i = 0; i < NV; ++i) r.g[i] = e * a.g[i]; return r; }
+Dual operator*(const Dual &a, real s) { Dual r; r.v = a.v * s; for (int i = 0; i < NV; ++i) r.g[i] = a.g[i] * s; return r; }
+Dual operator*(real s, const Dual &a) { return a * s; }
+Dual operator/(const Dual &a, real s) { return a * (1.0 / s); }
+Dual operator/(real s, const Dual &a) { return cst(s) / a; }
+Dual dexp(const Dual &a) { real e = std::exp(a.v); Dual r; r.v = e; for (int i = 0; i < NV; ++i) r.g[i] = e * a.g[i]; return r; }
 Dual dlog(const Dual &a) { Dual r; r.v = std::log(a.v); for (int i = 0; i < NV; ++i) r.g[i] = a.g[i] / a.v; return r; }
-Dual dsqrt(const Dual &a) { double s = std::sqrt(a.v); Dual r; r.v = s; for (int i = 0; i < NV; ++i) r.g[i] = a.g[i] / (2.0 * s); return r; }
-Dual dpow(const Dual &a, double p) { double v = std::pow(a.v, p); Dual r; r.v = v; double d = p * std::pow(a.v, p - 1.0); for (int i = 0; i < NV; ++i) r.g[i] = d * a.g[i]; return r; }
+Dual dsqrt(const Dual &a) { real s = std::sqrt(a.v); Dual r; r.v = s; for (int i = 0; i < NV; ++i) r.g[i] = a.g[i] / (2.0 * s); return r; }
+Dual dpow(const Dual &a, double p) { real v = std::pow(a.v, p); Dual r; r.v = v; real d = p * std::pow(a.v, p - 1.0); for (int i = 0; i < NV; ++i) r.g[i] = d * a.g[i]; return r; }
 Dual dlog10(const Dual &a) { return dlog(a) / std::log(10.0); }
 
 // ------------------------------------------------------------------ helpers
@@ -97,14 +111,14 @@ bool bit(uint32_t m, uint32_t b) { return (m & b) != 0; }
 bool rbit(const oracle_config &c, int i) { return (c.reaction_mask >> i) & 1u; }
 
 struct CellIn {      // per-cell inputs that the step does not evolve
-  double n;          // n_H
-  double G0, nEUV, NH2;
-  double Cd;         // C_d
-  double fd;         // f_d = Z / Zsun
-  double rho;        // gas density
+  real n;          // n_H
+  real G0, nEUV, NH2;
+  real Cd;         // C_d
+  real fd;         // f_d = Z / Zsun
+  real rho;        // gas density
 };
 
-CellIn make_cell(double n, double G0, double nEUV, double NH2, double cd_factor, const oracle_config &c) {
+CellIn make_cell(real n, real G0, real nEUV, real NH2, real cd_factor, const oracle_config &c) {
   CellIn ci;
   ci.n = n; ci.G0 = G0; ci.nEUV = nEUV; ci.NH2 = NH2;
   ci.Cd = cd_factor * C_d_unit;
@@ -119,7 +133,7 @@ void rates(const Dual &T, const Dual &Td, const CellIn &ci, const oracle_config 
   // H0: collisional ionization, polynomial in ln T_g(eV); reading: T(eV) = T/11604.5
   {
     Dual x = dlog(T / 11604.5);
-    const double a[9] = {-32.71396786, 13.536556, -5.73932875, 1.563154998, -0.2877056,
+    const real a[9] = {-32.71396786, 13.536556, -5.73932875, 1.563154998, -0.2877056,
                          3.48255977e-2, -2.63197617e-3, 1.11954395e-4, -2.03914985e-6};
     Dual p = cst(0.0), xp = cst(1.0);
     for (int i = 0; i < 9; ++i) { p = p + a[i] * xp; xp = xp * x; }
@@ -161,7 +175,7 @@ void rates(const Dual &T, const Dual &Td, const CellIn &ci, const oracle_config 
   k[9] = cst(c_light * sigma_EUV * ci.nEUV);
   // H10: stand-in photodissociation k_LW G0 f_sh(N_H2), power-law self-shielding
   {
-    double fsh = ci.NH2 > N_sh0 ? std::pow(ci.NH2 / N_sh0, -sh_pow) : 1.0;
+    real fsh = ci.NH2 > N_sh0 ? std::pow(ci.NH2 / N_sh0, -sh_pow) : 1.0;
     k[10] = cst(k_LW * ci.G0 * fsh);
   }
   // H11: stand-in cosmic-ray ionization
@@ -175,7 +189,7 @@ void rates(const Dual &T, const Dual &Td, const CellIn &ci, const oracle_config 
 // the H- channel forms H2 at k_H2 n y_H y_e and returns the electron.
 void chem_rates(const Dual &yH2, const Dual &ye, const Dual k[12], const CellIn &ci,
                 const oracle_config &c, Dual &RH2, Dual &Re) {
-  double n = ci.n;
+  real n = ci.n;
   Dual yH = 1.0 - 2.0 * yH2 - ye;   // H-nuclei conservation, y_H+ = y_e (Sec. 2.2.8)
   Dual yHp = ye;
   Dual via_Hm = (rbit(c, 2) && rbit(c, 3)) ? k[2] * n * yH * ye : cst(0.0);
@@ -185,14 +199,14 @@ void chem_rates(const Dual &yH2, const Dual &ye, const Dual k[12], const CellIn 
 }
 
 // ---------------- Table 4: heating minus cooling (volumetric), excluding gas-grain
-Dual line2(const Dual &T, double n, double x, double Tstar, double A, double g, double ncr, double fd) {
+Dual line2(const Dual &T, real n, real x, real Tstar, real A, real g, real ncr, real fd) {
   Dual e = g * dexp(-Tstar / T);
   return x * fd * n * (kB * Tstar) * A * e / (1.0 + e + ncr / n);
 }
 
 Dual gas_heat_cool(const Dual &yH2, const Dual &ye, const Dual &T, const Dual k[12],
                    const CellIn &ci, const oracle_config &c) {
-  double n = ci.n, n2 = n * n;
+  real n = ci.n, n2 = n * n;
   uint32_t m = c.process_mask;
   Dual yH = 1.0 - 2.0 * yH2 - ye, yHp = ye;
   Dual net = cst(0.0);
@@ -235,25 +249,25 @@ Dual gas_heat_cool(const Dual &yH2, const Dual &ye, const Dual &T, const Dual k[
 }
 
 // ----------------------------------------------------- Appendix C dust terms
-double kappa(double T) { return T < kap_Tc ? kap0 * (T / kap_T0) * (T / kap_T0) : kap0 * (kap_Tc / kap_T0) * (kap_Tc / kap_T0); }
-double dkappa(double T) { return T < kap_Tc ? 2.0 * kap0 * T / (kap_T0 * kap_T0) : 0.0; }
+real kappa(real T) { return T < kap_Tc ? kap0 * (T / kap_T0) * (T / kap_T0) : kap0 * (kap_Tc / kap_T0) * (kap_Tc / kap_T0); }
+real dkappa(real T) { return T < kap_Tc ? 2.0 * kap0 * T / (kap_T0 * kap_T0) : 0.0; }
 
 struct DustTerms {
-  double T_IR;         // a T_IR^4 = (c~/c) E_IR
-  double emit;         // kappa(T_d) a c T_d^4
-  double irabs;        // kappa(T_IR) c~ E_IR
-  double EUV;          // dust absorption of EUV+FUV
-  double G;            // R_g n_H sqrt(T_g / T_high), zero when gas-grain is off
-  double gam;          // gamma_d (Eq. ap_eq:gamma_d)
-  double zeta;         // Eq. ap_eq:zeta
-  double beta_d;       // Eq. ap_eq:beta_d
-  double beta_IR;      // Eq. ap_eq:beta_IR
-  double D;            // C_d dT_d/dt  (Eq. ap_eq:dust_temp)
-  double I;            // dE_IR/dt     (Eq. ap_eq:Eir)
-  double Qgg;          // de_th/dt from gas-grain transfer (Eq. ap_eq:Tg)
+  real T_IR;         // a T_IR^4 = (c~/c) E_IR
+  real emit;         // kappa(T_d) a c T_d^4
+  real irabs;        // kappa(T_IR) c~ E_IR
+  real EUV;          // dust absorption of EUV+FUV
+  real G;            // R_g n_H sqrt(T_g / T_high), zero when gas-grain is off
+  real gam;          // gamma_d (Eq. ap_eq:gamma_d)
+  real zeta;         // Eq. ap_eq:zeta
+  real beta_d;       // Eq. ap_eq:beta_d
+  real beta_IR;      // Eq. ap_eq:beta_IR
+  real D;            // C_d dT_d/dt  (Eq. ap_eq:dust_temp)
+  real I;            // dE_IR/dt     (Eq. ap_eq:Eir)
+  real Qgg;          // de_th/dt from gas-grain transfer (Eq. ap_eq:Tg)
 };
 
-DustTerms dust_terms(double Tg, double Td, double E, const CellIn &ci, const oracle_config &c) {
+DustTerms dust_terms(real Tg, real Td, real E, const CellIn &ci, const oracle_config &c) {
   DustTerms d;
   uint32_t m = c.process_mask;
   bool on_emit = bit(m, ORACLE_P_DUST_EMIT), on_irabs = bit(m, ORACLE_P_DUST_IRABS);
@@ -262,7 +276,7 @@ DustTerms dust_terms(double Tg, double Td, double E, const CellIn &ci, const ora
   d.emit = on_emit ? kappa(Td) * a_rad * c_light * std::pow(Td, 4) : 0.0;
   d.irabs = on_irabs ? kappa(d.T_IR) * c_red * E : 0.0;
   // stand-in: E_UV = c kappa_UV (u_FUV + u_EUV), kappa_UV per gas mass
-  double kap_UV = sigma_dUV / ((1.0 + 4.0 * y_He) * mH);
+  real kap_UV = sigma_dUV / ((1.0 + 4.0 * y_He) * mH);
   d.EUV = on_uv ? c_light * kap_UV * (ci.G0 * u_Habing + ci.nEUV * hnu_EUV) : 0.0;
   d.G = on_gg ? R_g * ci.n * std::sqrt(Tg / T_high) : 0.0;
   d.gam = 1.0 - 0.8 * std::exp(-T_low / Tg);
@@ -276,10 +290,10 @@ DustTerms dust_terms(double Tg, double Td, double E, const CellIn &ci, const ora
 }
 
 // --------------------------------------------------------------- gas state
-struct GasState { double ntot, mu, alpha_g, P; };
-GasState gas_state(double yH2, double ye, double Tg, const CellIn &ci, const oracle_config &c) {
+struct GasState { real ntot, mu, alpha_g, P; };
+GasState gas_state(real yH2, real ye, real Tg, const CellIn &ci, const oracle_config &c) {
   GasState s;
-  double yH = 1.0 - 2.0 * yH2 - ye;
+  real yH = 1.0 - 2.0 * yH2 - ye;
   s.ntot = ci.n * (yH + yH2 + ye + ye + y_He);                       // H, H2, H+, e, He
   s.mu = ci.rho / (s.ntot * mH);
   s.alpha_g = kB / ((c.gamma_ad - 1.0) * s.mu * mH);                  // Eq. ap_eq:alpha_g
@@ -289,19 +303,20 @@ GasState gas_state(double yH2, double ye, double Tg, const CellIn &ci, const ora
 
 // ------------------------------------------------ one LI substep's system
 struct System {
-  double F[5];      // right-hand sides (R_H2, R_e, q + Q_gg, D, I)
-  double J[5][5];   // dF/du (exact)
-  double M[5];      // 1, 1, alpha_g, C_d, 1
-  double ts[3];     // dt_dust, dt_chem, dt_energy
-  double aux[5];    // rho, alpha_g, E_UV, P, Gamma - Lambda (volumetric, incl. gas-grain)
+  real F[5];      // right-hand sides (R_H2, R_e, q + Q_gg, D, I)
+  real J[5][5];   // dF/du (exact)
+  real M[5];      // 1, 1, alpha_g, C_d, 1
+  real ts[3];     // dt_dust, dt_chem, dt_energy
+  real aux[5];    // rho, alpha_g, E_UV, P, Gamma - Lambda (volumetric, incl. gas-grain)
   DustTerms d;
 };
 
-double E_floor_of() { return (c_light / c_red) * a_rad * std::pow(T_CMB, 4); }
+real E_floor_of() { return (c_light / c_red) * a_rad * std::pow(T_CMB, 4); }
 
-double ratio_ts(double x, double rate) { return rate != 0.0 ? std::fabs(x) / std::fabs(rate) : INF; }
+real ratio_ts(real x, real rate) { return rate != 0.0 ? std::fabs(x) / std::fabs(rate) : INF; }
 
-System build_system(const double u[5], const CellIn &ci, const oracle_config &c) {
+System build_system(const real u[5], const CellIn &ci, const oracle_config &c) {
+  ORACLE_SECTION(0);
   System s;
   std::memset(&s, 0, sizeof(s));
   uint32_t fl = c.flags;
@@ -325,7 +340,7 @@ System build_system(const double u[5], const CellIn &ci, const oracle_config &c)
   s.J[2][2] += ci.fd * d.G * d.zeta;       // d/dT_g of Q_gg (the zeta term of Eq. ap_eq:Tg_2)
   s.J[2][3] += ci.fd * d.G * d.gam;        // d/dT_d of Q_gg
   // dust row (Eq. ap_eq:Td2) and IR row, coefficients of Appendix C
-  double acTd3 = a_rad * c_light * std::pow(u[3], 3);
+  real acTd3 = a_rad * c_light * std::pow(u[3], 3);
   s.F[3] = d.D;
   s.J[3][3] = -(d.G * d.gam + acTd3 * d.beta_d);
   s.J[3][4] = c_red * d.beta_IR;
@@ -339,30 +354,43 @@ System build_system(const double u[5], const CellIn &ci, const oracle_config &c)
     s.J[2][0] = s.J[2][1] = 0.0;
     s.J[2][3] -= q.g[3];
   }
-  double Cd = ci.Cd;
+  real Cd = ci.Cd;
   s.M[0] = 1.0; s.M[1] = 1.0; s.M[2] = gs.alpha_g; s.M[3] = Cd; s.M[4] = 1.0;
   // timescales (Eqs. timescale_of_dust, timescale_chemi, timescale_energy)
-  double tdust = INF;
+  real tdust = INF;
   if (!bit(fl, ORACLE_F_FREEZE_TD)) tdust = std::min(tdust, ratio_ts(u[3], d.D / Cd));
   if (!bit(fl, ORACLE_F_FREEZE_TG)) tdust = std::min(tdust, ratio_ts(u[2], d.Qgg / gs.alpha_g));
   if (!bit(fl, ORACLE_F_FREEZE_EIR)) tdust = std::min(tdust, ratio_ts(u[4], d.I));
-  double tchem = INF;
+  real tchem = INF;
   // reading: the abundance in Eq. timescale_chemi is floored at y_floor
   if (!bit(fl, ORACLE_F_FREEZE_YH2)) tchem = std::min(tchem, ratio_ts(std::max(u[0], c.y_floor), RH2.v));
   if (!bit(fl, ORACLE_F_FREEZE_YE)) tchem = std::min(tchem, ratio_ts(std::max(u[1], c.y_floor), Re.v));
-  double GmL = ci.rho * (q.v + d.Qgg);
-  double tener = INF;
+  real GmL = ci.rho * (q.v + d.Qgg);
+  real tener = INF;
   if (!bit(fl, ORACLE_F_FREEZE_TG)) tener = GmL != 0.0 ? gs.P / ((c.gamma_ad - 1.0) * std::fabs(GmL)) : INF;
   s.ts[0] = tdust; s.ts[1] = tchem; s.ts[2] = tener;
   s.aux[0] = ci.rho; s.aux[1] = gs.alpha_g; s.aux[2] = d.EUV; s.aux[3] = gs.P; s.aux[4] = GmL;
   return s;
 }
 
+// Test hook (0 = off, the default): every entry of each substep's system is
+// multiplied by 1 +- g_perturb in a fixed sign pattern, so that the tests
+// can measure how much a cell's result depends on rounding-level changes of
+// its linear systems (another implementation's different but equally valid
+// rounding of the rates and derivatives).
+double g_perturb = 0.0;
+
 // (M - dt J) du = dt F, with frozen variables' rows replaced by du_j = 0
-void assemble(const System &s, double dt, const oracle_config &c, double A[25], double b[5]) {
+void assemble(const System &s, real dt, const oracle_config &c, real A[25], real b[5]) {
   for (int r = 0; r < 5; ++r) {
     for (int j = 0; j < 5; ++j) A[r * 5 + j] = (r == j ? s.M[r] : 0.0) - dt * s.J[r][j];
     b[r] = dt * s.F[r];
+  }
+  if (g_perturb != 0.0) {
+    for (int r = 0; r < 5; ++r) {
+      for (int j = 0; j < 5; ++j) A[r * 5 + j] = A[r * 5 + j] * (1.0 + ((r * 7 + j * 3) % 2 ? g_perturb : -g_perturb));
+      b[r] = b[r] * (1.0 + (r % 2 ? -g_perturb : g_perturb));
+    }
   }
   const uint32_t fr[5] = {ORACLE_F_FREEZE_YH2, ORACLE_F_FREEZE_YE, ORACLE_F_FREEZE_TG,
                           ORACLE_F_FREEZE_TD, ORACLE_F_FREEZE_EIR};
@@ -377,12 +405,12 @@ void assemble(const System &s, double dt, const oracle_config &c, double A[25], 
 // lowest row index on ties) and back substitution, on a system that has
 // been equilibrated by powers of two (exact, no rounding): every column,
 // then every row, is scaled so that its largest entry lies in [0.5, 1).
-int ge_solve(int N, const double *Ain, const double *bin, double *x) {
-  double A[25], b[5], cs[5];
-  std::memcpy(A, Ain, sizeof(double) * N * N);
-  std::memcpy(b, bin, sizeof(double) * N);
+int ge_solve(int N, const real *Ain, const real *bin, real *x) {
+  real A[25], b[5], cs[5];
+  std::memcpy(A, Ain, sizeof(real) * N * N);
+  std::memcpy(b, bin, sizeof(real) * N);
   for (int j = 0; j < N; ++j) {
-    double m = 0.0;
+    real m = 0.0;
     for (int i = 0; i < N; ++i) m = std::max(m, std::fabs(A[i * N + j]));
     if (m == 0.0) return -1;
     int e;
@@ -391,12 +419,12 @@ int ge_solve(int N, const double *Ain, const double *bin, double *x) {
     for (int i = 0; i < N; ++i) A[i * N + j] *= cs[j];
   }
   for (int i = 0; i < N; ++i) {
-    double m = 0.0;
+    real m = 0.0;
     for (int j = 0; j < N; ++j) m = std::max(m, std::fabs(A[i * N + j]));
     if (m == 0.0) return -1;
     int e;
     std::frexp(m, &e);
-    double rs = std::ldexp(1.0, -e);
+    real rs = std::ldexp(1.0, -e);
     for (int j = 0; j < N; ++j) A[i * N + j] *= rs;
     b[i] *= rs;
   }
@@ -410,13 +438,13 @@ int ge_solve(int N, const double *Ain, const double *bin, double *x) {
       std::swap(b[p], b[col]);
     }
     for (int r = col + 1; r < N; ++r) {
-      double f = A[r * N + col] / A[col * N + col];
+      real f = A[r * N + col] / A[col * N + col];
       for (int j = col; j < N; ++j) A[r * N + j] -= f * A[col * N + j];
       b[r] -= f * b[col];
     }
   }
   for (int r = N - 1; r >= 0; --r) {
-    double s = b[r];
+    real s = b[r];
     for (int j = r + 1; j < N; ++j) s -= A[r * N + j] * x[j];
     x[r] = s / A[r * N + r];
   }
@@ -427,15 +455,15 @@ int ge_solve(int N, const double *Ain, const double *bin, double *x) {
 // r = b - A x with the products and sums carried exactly to twice the
 // working precision (error-free transformations: TwoProduct through fma,
 // TwoSum), rounded once at the end.
-void residual_dd(int N, const double *A, const double *b, const double *x, double *r) {
+void residual_dd(int N, const real *A, const real *b, const real *x, real *r) {
   for (int i = 0; i < N; ++i) {
-    double s = b[i], c = 0.0;
+    real s = b[i], c = 0.0;
     for (int j = 0; j < N; ++j) {
-      double p = -A[i * N + j] * x[j];
-      double pe = std::fma(-A[i * N + j], x[j], -p);   // exact error of the product
-      double t = s + p;
-      double z = t - s;
-      double se = (s - (t - z)) + (p - z);             // exact error of the sum
+      real p = -A[i * N + j] * x[j];
+      real pe = std::fma(-A[i * N + j], x[j], -p);   // exact error of the product
+      real t = s + p;
+      real z = t - s;
+      real se = (s - (t - z)) + (p - z);             // exact error of the sum
       s = t;
       c += pe + se;
     }
@@ -449,10 +477,11 @@ void residual_dd(int N, const double *A, const double *b, const double *x, doubl
 // temperature update) must come out with full relative accuracy, so the
 // equilibrated elimination is followed by two steps of iterative refinement
 // with residuals computed to twice the working precision.
-int solve_n(int N, const double *A, const double *b, double *x) {
+int solve_n(int N, const real *A, const real *b, real *x) {
+  ORACLE_SECTION(1);
   if (ge_solve(N, A, b, x) != 0) return -1;
   for (int it = 0; it < 2; ++it) {
-    double r[5], d[5];
+    real r[5], d[5];
     residual_dd(N, A, b, x, r);
     if (ge_solve(N, A, r, d) != 0) return -1;
     for (int j = 0; j < N; ++j) x[j] += d[j];
@@ -462,7 +491,7 @@ int solve_n(int N, const double *A, const double *b, double *x) {
 
 // abundance and floor projection after an update (reading of the positivity
 // rules, which the paper leaves open)
-void project(double u[5]) {
+void project(real u[5]) {
   u[1] = std::min(std::max(u[1], 0.0), 1.0);
   u[0] = std::min(std::max(u[0], 0.0), (1.0 - u[1]) / 2.0);
   u[2] = std::max(u[2], T_CMB);
@@ -473,8 +502,8 @@ void project(double u[5]) {
 // reading: a Newton correction (dT_d, dE_IR) of the tight-coupling iteration
 // is scaled by one factor lam <= 1 so that T_d changes by at most a factor 2
 // and E_IR (proportional to T_IR^4) by at most a factor 16 per iteration.
-double damp_factor(double Td, double E, double dTd, double dE) {
-  double lam = 1.0;
+real damp_factor(real Td, real E, real dTd, real dE) {
+  real lam = 1.0;
   if (Td + dTd > 2.0 * Td) lam = std::min(lam, Td / dTd);
   if (Td + dTd < 0.5 * Td) lam = std::min(lam, -0.5 * Td / dTd);
   if (E + dE > 16.0 * E) lam = std::min(lam, 15.0 * E / dE);
@@ -486,25 +515,26 @@ double damp_factor(double Td, double E, double dTd, double dE) {
 // chemistry (the tight-coupling iteration of Sec. 2.2.8; the NR solver's
 // group (ii)).  u holds the current iterate, u0 the step's start state.
 // Returns the iteration count, negative if the limit was reached.
-int newton_dust(double u[5], const double u0[5], double dt, const CellIn &ci, const oracle_config &c,
-                double tol, int limit) {
+int newton_dust(real u[5], const real u0[5], real dt, const CellIn &ci, const oracle_config &c,
+                real tol, int limit) {
+  ORACLE_SECTION(2);
   bool frTd = bit(c.flags, ORACLE_F_FREEZE_TD), frE = bit(c.flags, ORACLE_F_FREEZE_EIR);
   if (frTd && frE) return 0;
   bool polish = false;
   for (int it = 1; it <= limit + 1; ++it) {
     if (it > limit && !polish) break;
     DustTerms d = dust_terms(u[2], u[3], u[4], ci, c);
-    double acTd3 = a_rad * c_light * std::pow(u[3], 3);
-    double G4 = ci.Cd * (u[3] - u0[3]) - dt * d.D;
-    double G5 = (u[4] - u0[4]) - dt * d.I;
-    double J[4] = {ci.Cd + dt * (d.G * d.gam + acTd3 * d.beta_d), -dt * c_red * d.beta_IR,
+    real acTd3 = a_rad * c_light * std::pow(u[3], 3);
+    real G4 = ci.Cd * (u[3] - u0[3]) - dt * d.D;
+    real G5 = (u[4] - u0[4]) - dt * d.I;
+    real J[4] = {ci.Cd + dt * (d.G * d.gam + acTd3 * d.beta_d), -dt * c_red * d.beta_IR,
                    -dt * ci.rho * acTd3 * ci.fd * d.beta_d, 1.0 + dt * ci.rho * c_red * ci.fd * d.beta_IR};
-    double rhs[2] = {-G4, -G5};
+    real rhs[2] = {-G4, -G5};
     if (frTd) { J[0] = 1.0; J[1] = 0.0; rhs[0] = 0.0; }
     if (frE) { J[2] = 0.0; J[3] = 1.0; rhs[1] = 0.0; }
-    double del[2];
+    real del[2];
     if (solve_n(2, J, rhs, del) != 0) return -it;
-    double lam = polish ? 1.0 : damp_factor(u[3], u[4], del[0], del[1]);
+    real lam = polish ? 1.0 : damp_factor(u[3], u[4], del[0], del[1]);
     u[3] += lam * del[0];
     u[4] += lam * del[1];
     project(u);
@@ -529,45 +559,52 @@ bool valid_input(double n, double Tg, double Td, double E, double yH2, double ye
 
 // The LI step of one cell over dt_h (Sec. 2.2.8 "Time stepping").
 // rec (optional) receives 7 doubles per substep.
-struct LIOut { int nsub; int nitr; uint8_t status; };
+struct LIOut { int nsub; int nitr; uint8_t status; int nrej; int nhalv; };
 
-LIOut li_cell(double u[5], const CellIn &ci, double dt_h, const oracle_config &c, int max_rec, double *rec) {
-  LIOut o = {0, 0, 0};
+LIOut li_cell(real u[5], const CellIn &ci, real dt_h, const oracle_config &c, int max_rec, real *rec) {
+  ORACLE_SECTION(3);
+  LIOut o = {0, 0, 0, 0, 0};
   project(u);
   if (dt_h == 0.0) return o;
   // mode: estimated number of subcycles from the start state (reading: once per call)
   System s0 = build_system(u, ci, c);
-  bool tight = !(dt_h < (double)c.n_cyc * c.f_chem * s0.ts[0]);
+  bool tight = !(dt_h < (real)c.n_cyc * c.f_chem * s0.ts[0]);
   if (tight) o.status |= ORACLE_ST_TIGHT;
-  double t = 0.0;
+  real t = 0.0;
   while (true) {
     System s = build_system(u, ci, c);
-    double tmin = std::min(s.ts[1], s.ts[2]);
+    real tmin = std::min(s.ts[1], s.ts[2]);
     if (!tight) tmin = std::min(tmin, s.ts[0]);
-    double dtc = c.f_chem * tmin;                     // Eq. timestep_subcycle
-    double rem = dt_h - t;
+    real dtc = c.f_chem * tmin;                     // Eq. timestep_subcycle
+    real rem = dt_h - t;
     bool last = false;
-    double dts;
+    real dts;
     // reading: the last substep is truncated to the time left, and a sliver
     // below 1e-12 dt_hydro is merged into the substep before it
     if (dtc >= rem || rem - dtc <= 1e-12 * dt_h) { dts = rem; last = true; }
     else dts = dtc;
     if (!(dts > 0.0) || !std::isfinite(dts)) { o.status |= ORACLE_ST_BADSTEP; break; }
-    double A[25], b[5], du[5], u0[5];
+    real A[25], b[5], du[5], u0[5];
     std::memcpy(u0, u, sizeof(u0));
     // reading: the LI step rests on small changes (Delta y_j << y_j in the
     // derivation of Eq. eq_deq).  An update that changes y_H2 or y_e by more
     // than half of max(y, y_floor), or T_g by more than a factor 2, lies
     // outside that regime (a near-singular I - dt J at an unstable balance):
-    // the substep is redone with half the step, at most 30 times.
+    // the substep is redone with half the step, at most 30 times.  The flag
+    // ORACLE_F_NO_REJECT turns this reading off (the paper's controller as
+    // printed, Eq. timestep_subcycle).
     bool bad_solve = false;
+    const bool reject_on = !bit(c.flags, ORACLE_F_NO_REJECT);
     for (int halvings = 0;; ++halvings) {
       assemble(s, dts, c, A, b);
       if (solve_n(5, A, b, du) != 0) { bad_solve = true; break; }
       bool small = std::fabs(du[0]) <= 0.5 * std::max(u0[0], c.y_floor) &&
                    std::fabs(du[1]) <= 0.5 * std::max(u0[1], c.y_floor) &&
                    du[2] <= u0[2] && du[2] >= -0.5 * u0[2];
-      if (small || halvings >= 30) break;
+      if (small || halvings >= 30 || !reject_on) {
+        if (halvings > 0) { o.nrej++; o.nhalv += halvings; }
+        break;
+      }
       dts *= 0.5;
       last = false;
     }
@@ -577,7 +614,7 @@ LIOut li_cell(double u[5], const CellIn &ci, double dt_h, const oracle_config &c
     if (tight) {
       // reading: the Newton iteration starts from the LI update of (T_d, E_IR)
       // limited like a Newton correction (factor 2 in T_d, 16 in E_IR)
-      double lam = damp_factor(u0[3], u0[4], u[3] - u0[3], u[4] - u0[4]);
+      real lam = damp_factor(u0[3], u0[4], u[3] - u0[3], u[4] - u0[4]);
       if (lam < 1.0) {
         u[3] = u0[3] + lam * (u[3] - u0[3]);
         u[4] = u0[4] + lam * (u[4] - u0[4]);
@@ -589,7 +626,7 @@ LIOut li_cell(double u[5], const CellIn &ci, double dt_h, const oracle_config &c
     }
     t = last ? dt_h : t + dts;
     if (rec && o.nsub < max_rec) {
-      double *r = rec + 7 * o.nsub;
+      real *r = rec + 7 * o.nsub;
       r[0] = t; r[1] = dts; r[2] = u[0]; r[3] = u[1]; r[4] = u[2]; r[5] = u[3]; r[6] = u[4];
     }
     o.nsub++;
@@ -601,8 +638,8 @@ LIOut li_cell(double u[5], const CellIn &ci, double dt_h, const oracle_config &c
 
 // ------------------------------------------------------- NR reference (B.E.)
 // Group (iii): species at fixed (T_g, T_d).  Returns iterations, <0 on failure.
-int newton_species(double u[5], const double u0[5], double dt, const CellIn &ci, const oracle_config &c,
-                   double tol, int limit) {
+int newton_species(real u[5], const real u0[5], real dt, const CellIn &ci, const oracle_config &c,
+                   real tol, int limit) {
   bool fr0 = bit(c.flags, ORACLE_F_FREEZE_YH2), fr1 = bit(c.flags, ORACLE_F_FREEZE_YE);
   if (fr0 && fr1) return 0;
   for (int it = 1; it <= limit; ++it) {
@@ -611,12 +648,12 @@ int newton_species(double u[5], const double u0[5], double dt, const CellIn &ci,
     rates(T, Td, ci, c, k);
     Dual RH2, Re;
     chem_rates(yH2, ye, k, ci, c, RH2, Re);
-    double G[2] = {u[0] - u0[0] - dt * RH2.v, u[1] - u0[1] - dt * Re.v};
-    double J[4] = {1.0 - dt * RH2.g[0], -dt * RH2.g[1], -dt * Re.g[0], 1.0 - dt * Re.g[1]};
-    double rhs[2] = {-G[0], -G[1]};
+    real G[2] = {u[0] - u0[0] - dt * RH2.v, u[1] - u0[1] - dt * Re.v};
+    real J[4] = {1.0 - dt * RH2.g[0], -dt * RH2.g[1], -dt * Re.g[0], 1.0 - dt * Re.g[1]};
+    real rhs[2] = {-G[0], -G[1]};
     if (fr0) { J[0] = 1.0; J[1] = 0.0; rhs[0] = 0.0; }
     if (fr1) { J[2] = 0.0; J[3] = 1.0; rhs[1] = 0.0; }
-    double del[2];
+    real del[2];
     if (solve_n(2, J, rhs, del) != 0) return -it;
     u[0] += del[0];
     u[1] += del[1];
@@ -629,9 +666,9 @@ int newton_species(double u[5], const double u0[5], double dt, const CellIn &ci,
 
 // Inner solves at a trial T_g, then the gas-energy residual
 // g(T_g) = alpha_g^t (T_g - T_g^t) - dt [ (Gamma'-Lambda')/rho + Q_gg ].
-bool nr_inner(double Tg, const double u0[5], double dt, const CellIn &ci, const oracle_config &c,
-              double tol, int limit, double uo[5], double &g) {
-  std::memcpy(uo, u0, sizeof(double) * 5);
+bool nr_inner(real Tg, const real u0[5], real dt, const CellIn &ci, const oracle_config &c,
+              real tol, int limit, real uo[5], real &g) {
+  std::memcpy(uo, u0, sizeof(real) * 5);
   uo[2] = Tg;
   if (newton_dust(uo, u0, dt, ci, c, tol, limit) < 0) return false;
   if (newton_species(uo, u0, dt, ci, c, tol, limit) < 0) return false;
@@ -647,29 +684,29 @@ bool nr_inner(double Tg, const double u0[5], double dt, const CellIn &ci, const 
 
 // One backward-Euler step by nested Newton-Raphson; returns outer iterations
 // (>0) on convergence, <=0 on failure.
-int nr_be_step(double u[5], double dt, const CellIn &ci, const oracle_config &c) {
-  double u0[5];
+int nr_be_step(real u[5], real dt, const CellIn &ci, const oracle_config &c) {
+  real u0[5];
   std::memcpy(u0, u, sizeof(u0));
   int limit = c.nr_itr_limit;
-  double uo[5], g;
+  real uo[5], g;
   if (bit(c.flags, ORACLE_F_FREEZE_TG)) {
     if (!nr_inner(u0[2], u0, dt, ci, c, c.nr_tol, limit, uo, g)) return 0;
     std::memcpy(u, uo, sizeof(uo));
     return 1;
   }
-  double Tg = u0[2];
+  real Tg = u0[2];
   for (int it = 1; it <= limit; ++it) {
     // convergence criterion relaxed to 1e-3 after N_itr,limit / 2 iterations
-    double tol = (it > limit / 2) ? 1e-3 : c.nr_tol;
-    double h = 1e-4 * Tg;   // reading: central-difference step relative to T_g
-    double gp, gm;
-    double up[5], um[5];
+    real tol = (it > limit / 2) ? 1e-3 : c.nr_tol;
+    real h = 1e-4 * Tg;   // reading: central-difference step relative to T_g
+    real gp, gm;
+    real up[5], um[5];
     if (!nr_inner(Tg, u0, dt, ci, c, tol, limit, uo, g)) return 0;
     if (!nr_inner(Tg + h, u0, dt, ci, c, tol, limit, up, gp)) return 0;
     if (!nr_inner(Tg - h, u0, dt, ci, c, tol, limit, um, gm)) return 0;
-    double dg = (gp - gm) / (2.0 * h);
+    real dg = (gp - gm) / (2.0 * h);
     if (dg == 0.0 || !std::isfinite(dg)) return 0;
-    double Tn = std::max(Tg - g / dg, T_CMB);
+    real Tn = std::max(Tg - g / dg, T_CMB);
     bool conv = std::fabs(Tn - Tg) <= tol * Tn;
     Tg = Tn;
     if (conv) {
@@ -683,15 +720,15 @@ int nr_be_step(double u[5], double dt, const CellIn &ci, const oracle_config &c)
 
 // Sec. 2.2.8: dt_hydro first; on failure dt_sub = (dt_hydro - t_sub) / 2^i
 // with i = 1 initially, i-1 after a success and i+1 after a failure.
-LIOut nr_cell(double u[5], const CellIn &ci, double dt_h, const oracle_config &c) {
-  LIOut o = {0, 0, 0};
+LIOut nr_cell(real u[5], const CellIn &ci, real dt_h, const oracle_config &c) {
+  LIOut o = {0, 0, 0, 0, 0};
   project(u);
-  double t = 0.0;
+  real t = 0.0;
   int i = 0;
   int tries = 0;
   while (t < dt_h) {
-    double dts = (dt_h - t) / std::pow(2.0, i);
-    double uu[5];
+    real dts = (dt_h - t) / std::pow(2.0, i);
+    real uu[5];
     std::memcpy(uu, u, sizeof(uu));
     int it = nr_be_step(uu, dts, ci, c);
     ++tries;
@@ -733,9 +770,10 @@ void oracle_default_config(oracle_config *c) {
   c->nr_tol = 1e-5;
 }
 
+#ifndef SFCHEM_ORACLE_OPCOUNT   // the op-counting build defines its own entry point
 int oracle_li_cells(int64_t n, const double *n_H, double *T_g, double *T_d, double *E_IR,
                     double *y_H2, double *y_e, double *y_H, double *y_Hp, double *y_Hm,
-                    uint8_t *status, int32_t *n_sub, int32_t *n_itr, const double *G0,
+                    uint8_t *status, int32_t *n_sub, int32_t *n_itr, int32_t *n_rej, const double *G0,
                     const double *n_EUV, const double *N_H2, const double *dt, double cd_factor,
                     const oracle_config *cfg, int n_threads) {
   if (n < 0 || !n_H || !T_g || !T_d || !E_IR || !y_H2 || !y_e || !G0 || !n_EUV || !N_H2 || !dt) return -1;
@@ -746,7 +784,7 @@ int oracle_li_cells(int64_t n, const double *n_H, double *T_g, double *T_d, doub
 #pragma omp parallel for schedule(dynamic, 16)
 #endif
   for (int64_t i = 0; i < n; ++i) {
-    LIOut o = {0, 0, 0};
+    LIOut o = {0, 0, 0, 0, 0};
     double u[5] = {y_H2[i], y_e[i], T_g[i], T_d[i], E_IR[i]};
     if (!valid_input(n_H[i], T_g[i], T_d[i], E_IR[i], y_H2[i], y_e[i], G0[i], n_EUV[i], N_H2[i], dt[i])) {
       o.status = ORACLE_ST_BADINPUT;
@@ -773,6 +811,7 @@ int oracle_li_cells(int64_t n, const double *n_H, double *T_g, double *T_d, doub
     if (status) status[i] = o.status;
     if (n_sub) n_sub[i] = o.nsub;
     if (n_itr) n_itr[i] = o.nitr;
+    if (n_rej) { n_rej[2 * i] = o.nrej; n_rej[2 * i + 1] = o.nhalv; }
   }
   return 0;
 }
@@ -804,7 +843,7 @@ int oracle_nr_cells(int64_t n, const double *n_H, double *T_g, double *T_d, doub
 #pragma omp parallel for schedule(dynamic, 4)
 #endif
   for (int64_t i = 0; i < n; ++i) {
-    LIOut o = {0, 0, 0};
+    LIOut o = {0, 0, 0, 0, 0};
     if (!valid_input(n_H[i], T_g[i], T_d[i], E_IR[i], y_H2[i], y_e[i], G0[i], n_EUV[i], N_H2[i], dt[i])) {
       o.status = ORACLE_ST_BADINPUT;
     } else {
@@ -851,5 +890,52 @@ void oracle_rhs(double n_H, const double u[5], double G0, double n_EUV, double N
 }
 
 int oracle_solve5(const double A[25], const double b[5], double x[5]) { return solve_n(5, A, b, x); }
+
+void oracle_set_perturbation(double eps) { g_perturb = eps; }
+
+// Photon consumption after the update (reading of Sec. 2.2.8, "Radiation
+// components": the EUV and FUV photons of the step are absorbed once the
+// abundances and temperatures are updated); implicit in dt, so that no band
+// goes negative and n' + absorbed = n exactly.
+int oracle_photon_update(int64_t n, const double *n_H, const double *y_H2, const double *y_e, const double *G0,
+                         const double *n_EUV, const double *N_H2, const double *dt, double *G0_out,
+                         double *n_EUV_out, double *absorbed) {
+  if (n < 0 || !n_H || !y_H2 || !y_e || !G0 || !n_EUV || !N_H2 || !dt || !G0_out || !n_EUV_out) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    const double nh = n_H[i];
+    const double yH = std::max(1.0 - 2.0 * y_H2[i] - y_e[i], 0.0);
+    // EUV: photoionization of H (the stand-in cross-section of k_H9) and dust
+    const double lam_H = c_light * nh * sigma_EUV * yH;
+    const double lam_dE = c_light * nh * sigma_dUV;
+    // of n photons, n x / (1 + x) are absorbed and n / (1 + x) remain
+    // (x = lam dt); the smaller share is computed from its own formula and
+    // the other as the rest, so that both are accurate for thin and opaque cells
+    const double xE = (lam_H + lam_dE) * dt[i];
+    const double takeE = xE < 1.0 ? n_EUV[i] * (xE / (1.0 + xE)) : n_EUV[i] - n_EUV[i] / (1.0 + xE);
+    const double nE = xE < 1.0 ? n_EUV[i] - takeE : n_EUV[i] / (1.0 + xE);
+    // FUV: one photon per photodissociation (k_H10 per Habing unit over the
+    // photon density of one Habing unit) and dust
+    const double fsh = N_H2[i] > N_sh0 ? std::pow(N_H2[i] / N_sh0, -sh_pow) : 1.0;
+    const double lam_2 = k_LW * fsh * nh * y_H2[i] * hnu_FUV / u_Habing;
+    const double lam_dF = c_light * nh * sigma_dUV;
+    const double xF = (lam_2 + lam_dF) * dt[i];
+    const double takeF = xF < 1.0 ? G0[i] * (xF / (1.0 + xF)) : G0[i] - G0[i] / (1.0 + xF);
+    const double g = xF < 1.0 ? G0[i] - takeF : G0[i] / (1.0 + xF);
+    n_EUV_out[i] = nE;
+    G0_out[i] = g;
+    if (absorbed) {
+      const double dE = takeE;                               // EUV photons removed
+      const double dF = takeF * u_Habing / hnu_FUV;          // FUV photons removed
+      const double sE = lam_H + lam_dE, sF = lam_2 + lam_dF;
+      absorbed[4 * i + 0] = sE > 0.0 ? dE * lam_H / sE : 0.0;
+      absorbed[4 * i + 1] = sE > 0.0 ? dE * lam_dE / sE : 0.0;
+      absorbed[4 * i + 2] = sF > 0.0 ? dF * lam_2 / sF : 0.0;
+      absorbed[4 * i + 3] = sF > 0.0 ? dF * lam_dF / sF : 0.0;
+    }
+  }
+  return 0;
+}
+
+#endif  // SFCHEM_ORACLE_OPCOUNT
 
 }  // extern "C"

@@ -73,7 +73,8 @@ enum {
   ORACLE_F_FREEZE_EIR = 1u << 2,
   ORACLE_F_FREEZE_YH2 = 1u << 3,
   ORACLE_F_FREEZE_YE = 1u << 4,
-  ORACLE_F_SPLIT = 1u << 5
+  ORACLE_F_SPLIT = 1u << 5,
+  ORACLE_F_NO_REJECT = 1u << 6   /* paper-literal controller: no step rejection (reading R30 off) */
 };
 
 /* per-cell status bits */
@@ -88,12 +89,14 @@ enum {
 void oracle_default_config(oracle_config *cfg);
 
 /* LI step of n cells over dt[i] seconds each (in place on T_g, T_d, E_IR,
- * y_H2, y_e).  y_H, y_Hp, y_Hm, status, n_sub, n_itr may be NULL.
+ * y_H2, y_e).  y_H, y_Hp, y_Hm, status, n_sub, n_itr, n_rej may be NULL.
+ * n_rej[2*i] counts the substeps of cell i that the step-rejection reading
+ * redid with a smaller step, n_rej[2*i+1] the halvings they took.
  * n_threads <= 0 uses OpenMP's default.  Returns 0, or -1 on a bad argument. */
 int oracle_li_cells(int64_t n, const double *n_H, double *T_g, double *T_d,
                     double *E_IR, double *y_H2, double *y_e, double *y_H,
                     double *y_Hp, double *y_Hm, uint8_t *status,
-                    int32_t *n_sub, int32_t *n_itr, const double *G0,
+                    int32_t *n_sub, int32_t *n_itr, int32_t *n_rej, const double *G0,
                     const double *n_EUV, const double *N_H2, const double *dt,
                     double cd_factor, const oracle_config *cfg, int n_threads);
 
@@ -131,6 +134,32 @@ void oracle_system(double n_H, const double u[5], double G0, double n_EUV,
 void oracle_rhs(double n_H, const double u[5], double G0, double n_EUV,
                 double N_H2, double cd_factor, const oracle_config *cfg,
                 double dudt[5]);
+
+/* Photon consumption after the thermochemical update (Sec. 2.2.8,
+ * "Radiation components"; reading: the absorption of the step's EUV and FUV
+ * photons by the updated gas and dust, implicit over dt).  Per cell, with
+ * y_H = 1 - 2 y_H2 - y_e of the updated state:
+ *   EUV: loss rate per photon lam_E = c n_H (sigma_H y_H + sigma_d);
+ *        n_EUV' = n_EUV / (1 + lam_E dt) (of n photons n x/(1+x) are
+ *        absorbed, x = lam dt; the smaller share is formed from its own
+ *        formula, the other as the rest);
+ *   FUV: photon density N_F = G0 u_Habing / h nu_F; loss rate per photon
+ *        lam_F = k_LW f_sh(N_H2) n_H y_H2 h nu_F / u_Habing + c n_H sigma_d
+ *        (one photon per photodissociation); G0' = G0 / (1 + lam_F dt).
+ * The photons removed (n_EUV - n_EUV', N_F - N_F') are split between gas and
+ * dust in proportion to their loss rates: absorbed[4*i + 0..3] = (EUV by H,
+ * EUV by dust, FUV by H2, FUV by dust) in photons cm^-3 (may be NULL).  The
+ * stand-in constants are those of the rates (sigma_H, k_LW, f_sh) and of the
+ * dust UV absorption (sigma_d, u_Habing), with h nu_F = 12.4 eV. */
+int oracle_photon_update(int64_t n, const double *n_H, const double *y_H2, const double *y_e,
+                         const double *G0, const double *n_EUV, const double *N_H2, const double *dt,
+                         double *G0_out, double *n_EUV_out, double *absorbed);
+
+/* Test hook, 0 (off) by default: multiply every entry of each LI substep's
+ * linear system by 1 +- eps in a fixed sign pattern (a rounding-level change
+ * of the system), to measure how much a result depends on such changes.
+ * Global: set it before a call, not during one. */
+void oracle_set_perturbation(double eps);
 
 /* Solve a row-major 5x5 system: power-of-two row/column equilibration,
  * Gaussian elimination with partial pivoting, two refinement steps with
