@@ -101,15 +101,18 @@ enum {
   SFCHEM_F_FREEZE_YH2 = 1u << 3, /* hold y_H2 fixed */
   SFCHEM_F_FREEZE_YE = 1u << 4,  /* hold y_e fixed */
   SFCHEM_F_SPLIT = 1u << 5,      /* drop the chemistry <-> energy cross-derivatives */
-  SFCHEM_F_REFINE_FF = 1u << 6   /* mixed precision: form the refinement residual with error-free
+  SFCHEM_F_REFINE_FF = 1u << 6,  /* mixed precision: form the refinement residual with error-free
                                     FP32 transformations (about 48 bits) instead of FP64 */
+  SFCHEM_F_NO_REJECT = 1u << 7   /* the substep controller exactly as Eq. timestep_subcycle prints
+                                    it: no step rejection (see sfchem_stats_t.rejected_substeps) */
 };
 
 /* ------------------------------------------------------------------ types */
 typedef struct sfchem_ctx sfchem_ctx; /* opaque */
 
 /* Cell state.  n_H is read; T_gas, T_dust, E_IR, y_H2, y_e are read and
- * overwritten; y_H, y_Hp, y_Hm, status, n_sub are written when non-NULL.
+ * overwritten; y_H, y_Hp, y_Hm, status, n_sub, n_itr are written when
+ * non-NULL.
  * y_H = 1 - 2 y_H2 - y_e and y_Hp = y_e (H-nuclei conservation and charge
  * neutrality, Sec. 2.2.8); y_Hm = k_H2 y_e / k_H3 (H- equilibrium). */
 typedef struct {
@@ -124,6 +127,9 @@ typedef struct {
   double *y_Hm;        /* out: H- abundance (may be NULL) */
   uint8_t *status;     /* out: SFCHEM_CELL_* bits (may be NULL) */
   int32_t *n_sub;      /* out: substeps taken (may be NULL) */
+  int32_t *n_itr;      /* out: Newton iterations of the cell (may be NULL): the tight-coupling
+                          iterations of the LI method, the outer T_gas iterations of
+                          sfchem_step_nr; sfchem_step_host does not write it */
 } sfchem_state_t;
 
 /* Radiation inputs per cell (read only). */
@@ -164,6 +170,14 @@ typedef struct {
   uint64_t noconv_cells;    /* SFCHEM_CELL_NOCONV */
   uint64_t badinput_cells;  /* SFCHEM_CELL_BADINPUT */
   uint64_t badstep_cells;   /* SFCHEM_CELL_BADSTEP */
+  /* Step rejection (a reading of the small-change assumption behind Eq.
+   * eq_deq; the paper's controller has no such step): an update that moves
+   * y_H2 or y_e by more than half of max(y, y_floor), or T_gas by more than
+   * a factor 2, is redone with half the step, at most 30 times.
+   * rejected_substeps counts the substeps that were redone at least once,
+   * step_halvings the halvings they took (both 0 under SFCHEM_F_NO_REJECT). */
+  uint64_t rejected_substeps;
+  uint64_t step_halvings;
   uint32_t max_substeps;    /* largest n_sub of a cell */
   uint32_t reserved;
   double last_kernel_ms;    /* device time of the last call's solver kernel */
@@ -268,6 +282,55 @@ int sfchem_autotune(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_f
                     const int64_t *block_offset, const double *block_dt, int32_t n_blocks,
                     double cd_factor, void *stream);
 
+/* Photon consumption after the thermochemical update (Sec. 2.2.8,
+ * "Radiation components": the EUV and FUV photons of the step are absorbed
+ * once the abundances and temperatures have been updated; the paper gives
+ * the details in another paper, so this is a reading with stand-in
+ * constants).  Per cell, with y_H = 1 - 2 y_H2 - y_e of the UPDATED state
+ * (call it after sfchem_step on the same arrays): each band loses photons at
+ * a rate per photon lam, taken implicitly over dt_seconds,
+ *   EUV: lam = c n_H (sigma_H y_H + sigma_d),   n_euv_out = n_euv / (1 + lam dt)
+ *   FUV: lam = k_LW f_sh(N_H2) n_H y_H2 h nu_F / u_Habing + c n_H sigma_d,
+ *        G0_out = G0 / (1 + lam dt)
+ * (sigma_H: the cross-section of k_H9; k_LW f_sh: k_H10 per Habing unit, one
+ * photon per photodissociation; sigma_d, u_Habing: the dust UV absorption of
+ * Appendix C's E_UV; h nu_F = 12.4 eV), so that no band goes negative and
+ * the photons removed are the photons absorbed.  Reads state->n_H, y_H2,
+ * y_e and fields->G0_fuv, n_euv, N_H2 (device arrays of n_cells); writes
+ * G0_out and n_euv_out (device arrays of n_cells; they may be the fields'
+ * own arrays, for an in-place update) and, when not NULL, absorbed (4
+ * n_cells doubles: per cell the EUV photons absorbed by H and by dust and
+ * the FUV photons absorbed by H2 and by dust, photons cm^-3, split in
+ * proportion to the rates).  Asynchronous on `stream`; n_cells == 0 is a
+ * no-op; SFCHEM_EINVAL on a NULL or misaligned pointer, n_cells < 0 or
+ * dt_seconds < 0. */
+int sfchem_photon_update(const sfchem_state_t *state, const sfchem_fields_t *fields, int64_t n_cells,
+                         double dt_seconds, double *G0_out, double *n_euv_out, double *absorbed, void *stream);
+
+/* Cost-balanced partition of a block list across devices (Sec. 4: the
+ * thermochemical update runs independently on each device; the cells are
+ * independent, so a rank may take any contiguous range of blocks).  Splits
+ * the blocks [0, n_blocks) (block b holds cells [block_offset[b],
+ * block_offset[b+1]), a HOST array of n_blocks + 1 entries starting at 0)
+ * into n_parts contiguous ranges: part k takes blocks [cut[k], cut[k+1]),
+ * with cut[0] = 0 <= cut[1] <= ... <= cut[n_parts] = n_blocks (n_parts + 1
+ * entries, written by the call).  The largest part's cost is minimal among
+ * contiguous cuts (to a relative 1e-12), and so at most
+ * total / n_parts + the largest block's cost.  block_cost (n_blocks HOST
+ * doubles, >= 0; e.g. the previous call's substeps per block from
+ * sfchem_block_costs) gives the cost of each block; NULL weighs blocks by
+ * their cell counts, and a block of cost 0 by its cell count.  Host only,
+ * no device needed; SFCHEM_EINVAL on bad arguments. */
+int sfchem_partition(const int64_t *block_offset, const double *block_cost, int32_t n_blocks, int32_t n_parts,
+                     int32_t *cut);
+
+/* The per-block cost of the context's last batched call (sfchem_step_batched,
+ * sfchem_step_host or sfchem_autotune): the sum of n_sub over each block's
+ * cells, as float, into the HOST array cost (n_blocks entries, n_blocks being
+ * that schedule's block count; otherwise SFCHEM_EINVAL).  Synchronizes the
+ * device. */
+int sfchem_block_costs(sfchem_ctx *ctx, float *cost, int32_t n_blocks);
+
 /* Copy the accumulated statistics to *out (synchronizes the stream of the
  * last call). */
 int sfchem_stats(sfchem_ctx *ctx, sfchem_stats_t *out);
@@ -292,8 +355,12 @@ const char *sfchem_last_cuda_error(void);
  * sfchem_step_batched with a configuration instead of a context (cfg may be
  * NULL for the defaults).  It allocates nothing: its scratch (work counter,
  * statistics, the block tables and the chunk table) is one file-scope
- * __device__ array of 1,131,264 bytes that every GPU which loads the library
- * holds until the process exits.
+ * __device__ array of 1,131,264 bytes.  CUDA places the library's device
+ * code and this array on a GPU when the library first uses that GPU (with
+ * CUDA's default lazy loading, inside the first call that needs them) and
+ * keeps them until the process exits: the first call on a device may
+ * therefore grow the device footprint by the array and the kernels' code,
+ * and belongs in start-up; later calls do not.
  * Limits: at most SFCHEM_NOALLOC_MAX_BLOCKS blocks and at most
  * SFCHEM_NOALLOC_MAX_CHUNKS chunks of 64 cells (a block of s cells takes
  * ceil(s/64) chunks); larger schedules are refused with SFCHEM_EINVAL before
@@ -302,8 +369,11 @@ const char *sfchem_last_cuda_error(void);
  * before any stream capture.  All calls share the one array, which keeps the
  * previous call's contents (each call clears what must start at zero):
  * calls whose work overlaps on the GPU race on it, so issue them one after
- * another (one stream, or synchronised).  Statistics are not reported and
- * the blocks run in index order (no cost ordering across calls). */
+ * another (one stream, or synchronised).  block_offset and block_dt are
+ * read during the call: it waits until `stream` has copied them to the
+ * device (and so for the work queued on `stream` before it), after which
+ * the caller may reuse or free them.  Statistics are not reported and the
+ * blocks run in index order (no cost ordering across calls). */
 #define SFCHEM_NOALLOC_MAX_BLOCKS 4096
 #define SFCHEM_NOALLOC_MAX_CHUNKS 65536
 int sfchem_step_batched_noalloc(const sfchem_config_t *cfg, const sfchem_state_t *state,

@@ -27,10 +27,11 @@ OK, EINVAL, ENOTINIT, ECUDA, ETIMEOUT, ENOMEM = 0, 1, 2, 3, 4, 5
 CELL_CAP, CELL_BADINPUT, CELL_NOCONV, CELL_TIGHT, CELL_BADSTEP = 1, 2, 4, 8, 16
 P_ALL = (1 << 17) - 1
 F_FREEZE_TG, F_FREEZE_TD, F_FREEZE_EIR, F_FREEZE_YH2, F_FREEZE_YE, F_SPLIT, F_REFINE_FF = 1, 2, 4, 8, 16, 32, 64
+F_NO_REJECT = 128
 
 STATE_FIELDS = ("T_g", "T_d", "E_IR", "y_H2", "y_e")            # evolved in place
 INPUT_FIELDS = ("n_H", "G0", "n_EUV", "N_H2")                      # read only
-OUTPUT_FIELDS = ("y_H", "y_Hp", "y_Hm", "status", "n_sub")         # written when present
+OUTPUT_FIELDS = ("y_H", "y_Hp", "y_Hm", "status", "n_sub", "n_itr")  # written when present
 
 
 class SfchemError(RuntimeError):
@@ -54,7 +55,8 @@ class sfchem_config_t(ctypes.Structure):
 
 class sfchem_state_t(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in
-                ("n_H", "T_gas", "T_dust", "E_IR", "y_H2", "y_e", "y_H", "y_Hp", "y_Hm", "status", "n_sub")]
+                ("n_H", "T_gas", "T_dust", "E_IR", "y_H2", "y_e", "y_H", "y_Hp", "y_Hm", "status", "n_sub",
+                 "n_itr")]
 
 
 class sfchem_fields_t(ctypes.Structure):
@@ -64,7 +66,7 @@ class sfchem_fields_t(ctypes.Structure):
 class sfchem_stats_t(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("calls", "cells", "substeps", "newton_iters", "tight_cells", "capped_cells",
-                 "noconv_cells", "badinput_cells", "badstep_cells")] + [
+                 "noconv_cells", "badinput_cells", "badstep_cells", "rejected_substeps", "step_halvings")] + [
         ("max_substeps", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("last_kernel_ms", ctypes.c_double)]
 
 
@@ -79,7 +81,7 @@ EXPORTS = ("sfchem_config_default", "sfchem_config_validate", "sfchem_init", "sf
            "sfchem_step", "sfchem_step_nr", "sfchem_step_batched", "sfchem_set_launch", "sfchem_get_launch",
            "sfchem_autotune", "sfchem_stats", "sfchem_stats_reset", "sfchem_finalize",
            "sfchem_strerror", "sfchem_last_cuda_error", "sfchem_version", "sfchem_step_batched_noalloc",
-           "sfchem_step_host")
+           "sfchem_step_host", "sfchem_partition", "sfchem_block_costs", "sfchem_photon_update")
 # scratch limits of sfchem_step_batched_noalloc (include/sfchem.h)
 NOALLOC_MAX_BLOCKS, NOALLOC_MAX_CHUNKS = 4096, 65536
 
@@ -120,6 +122,9 @@ def lib():
                                               P(ctypes.c_int64), P(ctypes.c_double), i32, dbl, vp]
     L.sfchem_step_host.argtypes = [vp, P(sfchem_state_t), P(sfchem_fields_t), P(ctypes.c_int64),
                                    P(ctypes.c_double), i32, dbl, i64, vp]
+    L.sfchem_partition.argtypes = [P(ctypes.c_int64), P(ctypes.c_double), i32, i32, P(ctypes.c_int32)]
+    L.sfchem_photon_update.argtypes = [P(sfchem_state_t), P(sfchem_fields_t), i64, dbl, vp, vp, vp, vp]
+    L.sfchem_block_costs.argtypes = [vp, P(ctypes.c_float), i32]
     L.sfchem_stats.argtypes = [vp, P(sfchem_stats_t)]
     L.sfchem_stats_reset.argtypes = [vp]
     L.sfchem_finalize.argtypes = [vp]
@@ -175,12 +180,13 @@ def make_structs(cells: dict, n: int, cuda: bool = True):
             _check_tensor(k, cells[k], n, torch.float64, cuda)
     if cells.get("status") is not None:
         _check_tensor("status", cells["status"], n, torch.uint8, cuda)
-    if cells.get("n_sub") is not None:
-        _check_tensor("n_sub", cells["n_sub"], n, torch.int32, cuda)
+    for k in ("n_sub", "n_itr"):
+        if cells.get(k) is not None:
+            _check_tensor(k, cells[k], n, torch.int32, cuda)
     st = sfchem_state_t(
         _ptr(cells["n_H"]), _ptr(cells["T_g"]), _ptr(cells["T_d"]), _ptr(cells["E_IR"]),
         _ptr(cells["y_H2"]), _ptr(cells["y_e"]), _ptr(cells.get("y_H")), _ptr(cells.get("y_Hp")),
-        _ptr(cells.get("y_Hm")), _ptr(cells.get("status")), _ptr(cells.get("n_sub")))
+        _ptr(cells.get("y_Hm")), _ptr(cells.get("status")), _ptr(cells.get("n_sub")), _ptr(cells.get("n_itr")))
     fl = sfchem_fields_t(_ptr(cells["G0"]), _ptr(cells["n_EUV"]), _ptr(cells["N_H2"]))
     return st, fl
 
@@ -286,6 +292,14 @@ class Solver:
         _check(lib().sfchem_get_launch(self.handle, ctypes.byref(l)), "sfchem_get_launch")
         return {"threads_per_cta": l.threads_per_cta, "ctas_per_sm": l.ctas_per_sm, "chunk": l.chunk}
 
+    def block_costs(self, n_blocks: int):
+        """Per-block substep sums of the last batched call (numpy float32)."""
+        import numpy as np
+        out = np.zeros(n_blocks, np.float32)
+        _check(lib().sfchem_block_costs(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        int(n_blocks)), "sfchem_block_costs")
+        return out
+
     def stats(self) -> dict:
         s = sfchem_stats_t()
         _check(lib().sfchem_stats(self.handle, ctypes.byref(s)), "sfchem_stats")
@@ -293,6 +307,43 @@ class Solver:
 
     def stats_reset(self):
         _check(lib().sfchem_stats_reset(self.handle), "sfchem_stats_reset")
+
+
+def photon_update(cells: dict, dt: float, G0_out=None, n_euv_out=None, absorbed=None, stream=None):
+    """sfchem_photon_update on a dict of CUDA tensors (after a step on the same
+    dict): writes the absorbed bands into G0_out / n_euv_out (new tensors when
+    None; pass cells["G0"] / cells["n_EUV"] for an in-place update) and,
+    when given, the (n, 4) absorbed photon counts; returns (G0_out, n_euv_out)."""
+    import torch
+    n = cells["n_H"].numel()
+    st, fl = make_structs(cells, n)
+    G0_out = torch.empty_like(cells["G0"]) if G0_out is None else G0_out
+    n_euv_out = torch.empty_like(cells["n_EUV"]) if n_euv_out is None else n_euv_out
+    for name, t, m in (("G0_out", G0_out, n), ("n_euv_out", n_euv_out, n)):
+        _check_tensor(name, t, m, torch.float64)
+    if absorbed is not None:
+        _check_tensor("absorbed", absorbed, 4 * n, torch.float64)
+    _check(lib().sfchem_photon_update(ctypes.byref(st), ctypes.byref(fl), n, float(dt), _ptr(G0_out),
+                                      _ptr(n_euv_out), _ptr(absorbed), _stream_handle(stream)),
+           "sfchem_photon_update")
+    return G0_out, n_euv_out
+
+
+def partition(block_offset, n_parts: int, block_cost=None):
+    """sfchem_partition: cut the blocks into n_parts contiguous, cost-balanced
+    ranges; returns the n_parts + 1 block indices of the cuts (host only)."""
+    import numpy as np
+    off = np.ascontiguousarray(block_offset, dtype=np.int64)
+    nb = len(off) - 1
+    cost = None if block_cost is None else np.ascontiguousarray(block_cost, dtype=np.float64)
+    if cost is not None and len(cost) != nb:
+        raise ValueError("block_cost must have one entry per block")
+    cut = np.zeros(n_parts + 1, np.int32)
+    _check(lib().sfchem_partition(
+        off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        None if cost is None else cost.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nb, int(n_parts),
+        cut.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "sfchem_partition")
+    return cut
 
 
 def to_device(cells: dict, device="cuda", outputs: bool = True) -> dict:
@@ -306,6 +357,7 @@ def to_device(cells: dict, device="cuda", outputs: bool = True) -> dict:
             out[k] = torch.empty(n, dtype=torch.float64, device=device)
         out["status"] = torch.empty(n, dtype=torch.uint8, device=device)
         out["n_sub"] = torch.empty(n, dtype=torch.int32, device=device)
+        out["n_itr"] = torch.empty(n, dtype=torch.int32, device=device)
     return out
 
 

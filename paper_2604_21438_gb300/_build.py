@@ -1,6 +1,6 @@
 """In-tree build of libsfchem.so (nvcc, sm_103a only).
 
-The three translation units are compiled in parallel and linked into one
+The translation units are compiled in parallel and linked into one
 shared library next to this file.  Rebuilds only when a source is newer than
 the library.
 """
@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsfchem.so")
 BENCH_LIB = os.path.join(HERE, "libsfbench.so")
-UNITS = ("li_fp64.cu", "li_mixed.cu", "nr_fp64.cu", "sfchem_abi.cu", "noalloc.cu")
+UNITS = ("li_fp64.cu", "li_mixed.cu", "li_mixed_ff.cu", "li_mixed_masked.cu", "nr_fp64.cu", "sfchem_abi.cu",
+         "noalloc.cu", "photon.cu")
 BENCH_UNITS = ("microbench.cu",)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]

@@ -8,6 +8,11 @@ cudaError_t launch_li_fp64(const KArgs &a, int grid, int tpb, cudaStream_t s);
 cudaError_t launch_li_mixed(const KArgs &a, int grid, int tpb, cudaStream_t s);
 cudaError_t occupancy_li_fp64(int tpb, int *ctas_per_sm);
 cudaError_t occupancy_li_mixed(int tpb, int *ctas_per_sm);
+// the instances behind launch_li_mixed (li_mixed_ff.cu, li_mixed_masked.cu)
+cudaError_t launch_li_mixed_ff(const KArgs &a, int grid, int tpb, cudaStream_t s);
+cudaError_t launch_li_mixed_masked(const KArgs &a, int grid, int tpb, cudaStream_t s);
+cudaError_t occupancy_li_mixed_ff(int tpb, int *ctas_per_sm);
+cudaError_t occupancy_li_mixed_masked(int tpb, int *ctas_per_sm);
 cudaError_t launch_nr_fp64(const KArgs &a, int grid, int tpb, cudaStream_t s);
 cudaError_t occupancy_nr_fp64(int tpb, int *ctas_per_sm);
 // One-CTA schedule kernel of the batched path (cost order and chunk table).

@@ -62,7 +62,7 @@ constexpr uint32_t P_L9 = 1u << 8, P_L10 = 1u << 9, P_L11 = 1u << 10, P_L12 = 1u
 constexpr uint32_t P_L13 = 1u << 12, P_GG = 1u << 13, P_UV = 1u << 14, P_EMIT = 1u << 15,
                    P_IRABS = 1u << 16;
 constexpr uint32_t F_FTG = 1u << 0, F_FTD = 1u << 1, F_FE = 1u << 2, F_FY2 = 1u << 3,
-                   F_FYE = 1u << 4, F_SPLIT = 1u << 5, F_REFINE_FF = 1u << 6;
+                   F_FYE = 1u << 4, F_SPLIT = 1u << 5, F_REFINE_FF = 1u << 6, F_NO_REJECT = 1u << 7;
 constexpr uint32_t R_ALL = (1u << 12) - 1u, P_ALL = (1u << 17) - 1u;   // every reaction / process
 constexpr uint8_t ST_CAP = 1, ST_BAD = 2, ST_NOCONV = 4, ST_TIGHT = 8, ST_BADSTEP = 16;
 
@@ -175,6 +175,12 @@ template <> __device__ __forceinline__ double to_w<double>(double d) { return d;
 template <> __device__ __forceinline__ float to_w<float>(double d) { return d2f_int(d); }
 __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return f2d_int(x); }
+
+// a / b: IEEE division in FP64; in FP32 a times the corrected reciprocal
+// (within 2 ulp, and a fraction of the instructions of an IEEE division),
+// for b > 0 finite
+__device__ __forceinline__ double div_w(double a, double b) { return a / b; }
+__device__ __forceinline__ float div_w(float a, float b) { return a * M<float>::rcp(b); }
 
 __device__ __forceinline__ double fmax_w(double a, double b) { return ::fmax(a, b); }
 __device__ __forceinline__ float fmax_w(float a, float b) { return ::fmaxf(a, b); }
@@ -436,6 +442,7 @@ template <typename W> struct Sys {
   W rate_dust, rate_chem, rate_energy;
   W H;   // (Gamma - Lambda) / (n_H k_B), gas-grain transfer included, unscaled
   W uf[5];   // the state as seen by this evaluation (rounded to W)
+  W uyH;     // y_H = 1 - 2 y_H2 - y_e, formed in FP64 and rounded to W
   W dTdg;    // T_d - T_g, formed in FP64 and rounded to W
 };
 
@@ -479,6 +486,7 @@ __device__ __forceinline__ void eval_system(const double u[5], double yH64, cons
   // (fully molecular or ionized gas; yH64 = 1 - 2 y_H2 - y_e, formed by the
   // caller) and T_d - T_g in tight gas-dust coupling
   const W yH = to_w<W>(yH64);
+  S.uyH = yH;
   const W dTdg = to_w<W>(u[3] - u[2]);
   S.dTdg = dTdg;
   const bool via_on = ((cfg.rmask >> 2) & 1u) && ((cfg.rmask >> 3) & 1u);
@@ -651,8 +659,8 @@ __device__ __forceinline__ void eval_system(const double u[5], double yH64, cons
   if (!(fl & F_FTG)) rd = fmax_w(rd, m::abs(hs * Hgg));
   if (!(fl & F_FE)) rd = fmax_w(rd, m::abs(S.F[4]));
   W rc = W(0);
-  if (!(fl & F_FY2)) rc = m::abs(S.F[0]) / fmax_w(y2, cw.y_floor);
-  if (!(fl & F_FYE)) rc = fmax_w(rc, m::abs(S.F[1]) / fmax_w(ye, cw.y_floor));
+  if (!(fl & F_FY2)) rc = div_w(m::abs(S.F[0]), fmax_w(y2, cw.y_floor));
+  if (!(fl & F_FYE)) rc = fmax_w(rc, div_w(m::abs(S.F[1]), fmax_w(ye, cw.y_floor)));
   S.rate_dust = rd;
   S.rate_chem = rc;
   S.rate_energy = (fl & F_FTG) ? W(0) : m::abs(S.F[2]);

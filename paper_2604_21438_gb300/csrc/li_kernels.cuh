@@ -15,24 +15,55 @@
 namespace sfc {
 
 // ------------------------------------------------------------------- 5x5 LU
-// Gaussian elimination with partial pivoting (largest |a| in the column, the
-// first such row on ties) on the fixed structure of A = I - dt J: rows 0-2
-// (y_H2, y_e, T_g) have non-zeros in columns 0-3, row 3 (T_d) in columns 2-4,
-// row 4 (E_IR) in columns 3-4.  A structural zero never wins a pivot search
-// and eliminating against it changes nothing, so only the candidate rows and
-// the non-zero columns are visited: the factors are those of the dense
-// elimination.  Row exchanges touch only the active columns, and the
-// multipliers stay where they were computed, so a second right-hand side is
-// solved by replaying the same exchanges (bits of sw) and eliminations.
+// Gaussian elimination with scaled partial pivoting on the fixed structure of
+// A = I - dt J: rows 0-2 (y_H2, y_e, T_g) have non-zeros in columns 0-3, row
+// 3 (T_d) in columns 2-4, row 4 (E_IR) in columns 3-4.  The pivot of a
+// column is the candidate with the largest |a| after each row of A is scaled
+// by the power of two that brings its largest entry into [1, 2) (the first
+// such row on ties): the choice of partial pivoting on the row-equilibrated
+// matrix, while the arithmetic stays on the unscaled rows.  Plain partial
+// pivoting lets a row dominated by its own diagonal win a column it barely
+// depends on -- the T_g row (entries ~1e2 in the abundance columns of hot
+// ionized gas) or the T_d row (diagonal ~1e5, T_g entry ~3 in tight
+// coupling) -- and the unknown of that column is then recovered from it by a
+// cancellation of up to ~1e11, losing most of its digits.  A structural zero
+// never wins a pivot search and eliminating against it changes nothing, so
+// only the candidate rows and the non-zero columns are visited: the factors
+// are those of the dense elimination.  Row exchanges touch only the active
+// columns, and the multipliers stay where they were computed, so a second
+// right-hand side is solved by replaying the same exchanges (bits of sw) and
+// eliminations.
 template <typename W> struct LU5 {
   W a[5][5];
   W inv[5];
   uint32_t sw;
 };
 
+// The biased exponent field of |x| (integer instructions, sign dropped) and
+// the power of two 2^-e for a row whose largest entry lies in [2^e, 2^(e+1)):
+// exact scalings that never overflow.  A row of zeros or subnormals gets the
+// largest factor; a row whose largest entry has the top finite exponent gets
+// 0, one holding an infinity or a NaN -inf, so that neither wins a pivot over
+// a finite row (such a system ends as a bad substep at its pivot test or in
+// the non-finite update anyway).
+__device__ __forceinline__ int expo_field(float x) { return __float_as_int(x) & 0x7f800000; }
+__device__ __forceinline__ int expo_field(double x) { return __double2hiint(x) & 0x7ff00000; }
+__device__ __forceinline__ void row_scale(int e, float &s) { s = __int_as_float(0x7f000000 - e); }
+__device__ __forceinline__ void row_scale(int e, double &s) { s = __hiloint2double(0x7fe00000 - e, 0); }
+
 template <typename W>
-__device__ __forceinline__ void lu5_swap(LU5<W> &L, int p, int r, int j0, int j1, int bit) {
-  const bool ex = M<W>::abs(L.a[r][p]) > M<W>::abs(L.a[p][p]);
+__device__ __forceinline__ W lu5_row_scale(const LU5<W> &L, int r, int j0, int j1) {
+  int e = 0;
+#pragma unroll
+  for (int j = j0; j < j1; ++j) e = max(e, expo_field(L.a[r][j]));
+  W s;
+  row_scale(e, s);
+  return s;
+}
+
+template <typename W>
+__device__ __forceinline__ void lu5_swap(LU5<W> &L, W rs[5], int p, int r, int j0, int j1, int bit) {
+  const bool ex = M<W>::abs(L.a[r][p]) * rs[r] > M<W>::abs(L.a[p][p]) * rs[p];
   L.sw |= (ex ? 1u : 0u) << bit;
 #pragma unroll
   for (int j = j0; j < j1; ++j) {
@@ -40,6 +71,9 @@ __device__ __forceinline__ void lu5_swap(LU5<W> &L, int p, int r, int j0, int j1
     L.a[p][j] = ex ? y : x;
     L.a[r][j] = ex ? x : y;
   }
+  const W sp = rs[p], sr = rs[r];
+  rs[p] = ex ? sr : sp;
+  rs[r] = ex ? sp : sr;
 }
 
 template <typename W>
@@ -61,22 +95,24 @@ __device__ __forceinline__ void lu5_elim(LU5<W> &L, int p, int r, int j1) {
 template <typename W>
 __device__ __forceinline__ bool lu5_factor(LU5<W> &L) {
   L.sw = 0u;
+  W rs[5] = {lu5_row_scale(L, 0, 0, 4), lu5_row_scale(L, 1, 0, 4), lu5_row_scale(L, 2, 0, 4),
+             lu5_row_scale(L, 3, 2, 5), lu5_row_scale(L, 4, 3, 5)};
   // column 0: candidates rows 1, 2 (columns 0-3)
-  lu5_swap(L, 0, 1, 0, 4, 0);
-  lu5_swap(L, 0, 2, 0, 4, 1);
+  lu5_swap(L, rs, 0, 1, 0, 4, 0);
+  lu5_swap(L, rs, 0, 2, 0, 4, 1);
   if (!lu5_pivot(L, 0)) return false;
   lu5_elim(L, 0, 1, 4);
   lu5_elim(L, 0, 2, 4);
   // column 1: candidate row 2 (columns 1-3)
-  lu5_swap(L, 1, 2, 1, 4, 2);
+  lu5_swap(L, rs, 1, 2, 1, 4, 2);
   if (!lu5_pivot(L, 1)) return false;
   lu5_elim(L, 1, 2, 4);
   // column 2: candidate row 3 (columns 2-4; row 2 is zero in column 4)
-  lu5_swap(L, 2, 3, 2, 5, 3);
+  lu5_swap(L, rs, 2, 3, 2, 5, 3);
   if (!lu5_pivot(L, 2)) return false;
   lu5_elim(L, 2, 3, 5);
   // column 3: candidate row 4 (columns 3-4)
-  lu5_swap(L, 3, 4, 3, 5, 4);
+  lu5_swap(L, rs, 3, 4, 3, 5, 4);
   if (!lu5_pivot(L, 3)) return false;
   lu5_elim(L, 3, 4, 5);
   return lu5_pivot(L, 4);
@@ -152,10 +188,12 @@ __device__ __forceinline__ void project(double u[5]) {
 template <typename W>
 __device__ __forceinline__ W damp_factor(W Td, W E, W dTd, W dE) {
   W lam = W(1);
-  if (Td + dTd > W(2) * Td) lam = min(lam, Td / dTd);
-  if (Td + dTd < W(0.5) * Td) lam = min(lam, W(-0.5) * Td / dTd);
-  if (E + dE > W(16) * E) lam = min(lam, W(15) * E / dE);
-  if (E + dE < E / W(16)) lam = min(lam, W(-15.0 / 16.0) * E / dE);
+  // (each division runs only where its condition holds, so its divisor is
+  // non-zero there)
+  if (Td + dTd > W(2) * Td) lam = min(lam, div_w(Td, dTd));
+  if (Td + dTd < W(0.5) * Td) lam = min(lam, div_w(W(-0.5) * Td, dTd));
+  if (E + dE > W(16) * E) lam = min(lam, div_w(W(15) * E, dE));
+  if (E + dE < E * W(0.0625)) lam = min(lam, div_w(W(-15.0 / 16.0) * E, dE));
   return lam;
 }
 
@@ -236,6 +274,13 @@ __device__ __forceinline__ int newton_dust(double u[5], const double u0[5], doub
   return it;
 }
 
+// Per-launch statistics (device), reduced per warp except the rare
+// step-rejection counts, which are added where they happen.
+struct DevStats {
+  unsigned long long cells, substeps, newton, tight, cap, noconv, bad, badstep, rejected, halvings;
+  unsigned int max_sub, pad;
+};
+
 // ------------------------------------------------------------- one cell
 template <typename W> struct CellRun {
   double u[5];   // y_H2, y_e, T_g, T_d, E_IR
@@ -293,13 +338,75 @@ __device__ __forceinline__ float residual_ff(float b, const float *a, const floa
   return s + c;
 }
 
+// Abundance rows of the mixed path in FP64, for the lanes whose update
+// cancels an abundance.  The substep's rate coefficients are evaluated again
+// (the same FP32 operations on the same inputs give the same values); the
+// chemistry rows -- R_H2, R_e and their partials in y_H2 and y_e (Eq. eq_deq)
+// -- are formed from them in FP64, with y_H = 1 - 2 y_H2 - y_e from the FP64
+// state.  The residual of those two rows, r = dt F - A x (their temperature
+// columns as in the FP32 system), is solved with the FP32 factors for a
+// correction d; with rows 2-4 left at their (refined) residual, x + d solves
+// the system whose chemistry rows are the FP64 ones.  Out of line, and every
+// argument by value: a reference would give the caller's registers an
+// address and move them to local memory for the whole loop.
+struct F5 { float v[5]; };
+struct PreciseOut { double inc0, inc1; float d2, d3, d4; };
+static __device__ __noinline__ PreciseOut precise_abundance_rows(
+    double y2, double ye, double yH64, float T, float Td, float n, float fd, float lnn, float k9, float k10,
+    float k11, uint32_t rmask, uint32_t flags, float dw, LU5<float> L, F5 x, F5 dx, float J02, float J03,
+    float J12, float J13) {
+  CellK<float> ck;
+  ck.n = n; ck.fd = fd; ck.lnn = lnn; ck.k9 = k9; ck.k10 = k10; ck.k11 = k11;
+  Pre<float> q;
+  make_pre<float>(T, Td, q);
+  Rates<float> r;
+  eval_rates<float>(T, Td, q, ck, rmask, r);
+  Rates<double> r64;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    r64.k[i] = f2d_int(r.k[i]);
+    r64.kT[i] = 0.0;
+  }
+  r64.k8d = 0.0;
+  const bool via_on = ((rmask >> 2) & 1u) && ((rmask >> 3) & 1u);
+  double F[2], Jr[2][4];
+  chem_rows<double>(r64, f2d_int(n), y2, ye, yH64, via_on, F[0], F[1], Jr[0], Jr[1], false);
+  const double dt = f2d_int(dw);
+  double X[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) X[j] = f2d_int(x.v[j]) + f2d_int(dx.v[j]);
+  const float Jt[2][2] = {{J02, J03}, {J12, J13}};
+  const uint32_t frozen[2] = {F_FY2, F_FYE};
+  float rr[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    if (flags & frozen[i]) continue;          // a frozen row is the identity: x_i = 0
+    double acc = dt * F[i];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc = fma(-((i == j ? 1.0 : 0.0) - dt * Jr[i][j]), X[j], acc);
+#pragma unroll
+    for (int j = 2; j < 4; ++j) acc = fma(-f2d_int(-dw * Jt[i][j - 2]), X[j], acc);
+    rr[i] = d2f_int(acc);
+  }
+  lu5_solve<float, float>(L, rr);
+  PreciseOut o;
+  o.inc0 = X[0] + f2d_int(rr[0]);
+  o.inc1 = X[1] + f2d_int(rr[1]);
+  o.d2 = rr[2]; o.d3 = rr[3]; o.d4 = rr[4];
+  return o;
+}
+
 // One LI substep of Sec. 2.2.8; returns true when the cell is finished.
 // MIXED: W = float for rates, Jacobian and LU, followed by one residual
 // refinement of the 5x5 solve (residual in FP64, or with error-free FP32
 // transformations when F_REFINE_FF is set); the update, the projection and the
 // time accounting stay FP64.
-template <typename W, bool MIXED>
-__device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, const CfgW<W> &cw) {
+// RF: how the mixed path forms its refinement residual -- -1 at run time
+// from SFCHEM_F_REFINE_FF, 0 the default (FP64 abundance rows), 1 every row
+// with error-free FP32 (a compile-time choice keeps one variant in the loop).
+template <typename W, bool MIXED, int RF = -1>
+__device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, const CfgW<W> &cw,
+                                           DevStats *stats) {
   Sys<W> S;
   double yH;
   if constexpr (MIXED) {
@@ -325,7 +432,8 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
   }
   W inv = fmax_w(S.rate_chem, S.rate_energy);
   if (c.mode == 0) inv = fmax_w(inv, S.rate_dust);
-  const W dtcw = cw.f_chem / inv;                   // +inf when every rate vanishes
+  // +inf when every rate vanishes; NaN rates give NaN (a bad substep below)
+  const W dtcw = inv == W(0) ? W(INFINITY) : div_w(cw.f_chem, inv);
   const double dtc = to_f64(dtcw);
   // time left: the FP64 path keeps the elapsed time (the oracle's order of
   // operations), the mixed path the time left itself (one FP64 add less)
@@ -377,29 +485,61 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
     // one refinement pass against the factored system (A, b): non-zeros of
     // A are rows 0-2 x columns 0-3, row 3 x columns 2-4, row 4 x columns 3-4
     // (A is re-formed from J: the same FP32 operations give the same entries)
+    // The residual of the two abundance rows is formed in FP64 (they feed
+    // y_H = 1 - 2 y_H2 - y_e, which cancels as the gas turns fully molecular
+    // or ionized); the three thermal rows, whose unknowns are relative
+    // changes, take the error-free FP32 residual (TwoProduct by fma, TwoSum:
+    // about 48 bits, the FP64 pipe being this kernel's scarce unit).
+    // F_REFINE_FF forms every row's residual the error-free FP32 way.
     const int j0[5] = {0, 0, 0, 2, 3}, j1[5] = {4, 4, 4, 5, 5};
+    const bool ff_all = RF < 0 ? (cfg.flags & F_REFINE_FF) != 0u : RF == 1;
     W r[5];
-    if (cfg.flags & F_REFINE_FF) {
 #pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        W Ai[5];
+    for (int i = 0; i < 5; ++i) {
+      W Ai[5];
 #pragma unroll
-        for (int j = 0; j < 5; ++j) Ai[j] = (i == j ? W(1) : W(0)) - dw * S.J[i][j];
-        r[i] = residual_ff(float(b[i]), (const float *)Ai, (const float *)x, j0[i], j1[i]);
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
+      for (int j = 0; j < 5; ++j) Ai[j] = (i == j ? W(1) : W(0)) - dw * S.J[i][j];
+      if (i < 2 && !ff_all) {
         double acc = to_f64(b[i]);
 #pragma unroll
-        for (int j = j0[i]; j < j1[i]; ++j)
-          acc = fma(-to_f64((i == j ? W(1) : W(0)) - dw * S.J[i][j]), to_f64(x[j]), acc);
+        for (int j = j0[i]; j < j1[i]; ++j) acc = fma(-to_f64(Ai[j]), to_f64(x[j]), acc);
         r[i] = to_w<W>(acc);
+      } else {
+        r[i] = residual_ff(float(b[i]), (const float *)Ai, (const float *)x, j0[i], j1[i]);
       }
     }
     lu5_solve<W, W>(L, r);
 #pragma unroll
     for (int i = 0; i < 5; ++i) dx[i] = r[i];
+  }
+  double inc0 = to_f64(x[0]) + to_f64(dx[0]), inc1 = to_f64(x[1]) + to_f64(dx[1]);
+  if constexpr (MIXED) {
+    // The increments come from FP32 rows and carry an absolute error of
+    // ~1e-7 of themselves.  Where an abundance's increment (for y_H, the two
+    // increments it is formed from) exceeds 64x the abundance's new value,
+    // that error is a relative one of up to ~4e-6 and more: a species driven
+    // towards 0, or y_H kept small while H2 and electrons trade places.
+    // Those lanes form the abundance rows again in FP64
+    // (precise_abundance_rows above).  Measured: about 1 lane-substep in 1e4
+    // on the GMC-like grid, 1 in 80 on uniform random cells; 8x instead of
+    // 64x triggers 15x more often for the same error.
+    const W e0 = x[0] + dx[0], e1 = x[1] + dx[1];
+    const W a0 = m_abs(e0), a1 = m_abs(e1);
+    const bool cancel = (W(2) * a0 + a1 > W(64) * (S.uyH - W(2) * e0 - e1)) || (a0 > W(64) * (S.uf[0] + e0)) ||
+                        (a1 > W(64) * (S.uf[1] + e1));
+    if (cancel) {
+      F5 xv, dxv;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) { xv.v[i] = x[i]; dxv.v[i] = dx[i]; }
+      const PreciseOut o = precise_abundance_rows(
+          c.u[0], c.u[1], yH, S.uf[2], S.uf[3], c.k.n, c.k.fd, c.k.lnn, c.k.k9, c.k.k10, c.k.k11, cfg.rmask,
+          cfg.flags, dw, L, xv, dxv, S.J[0][2], S.J[0][3], S.J[1][2], S.J[1][3]);
+      inc0 = o.inc0;
+      inc1 = o.inc1;
+      x[2] += o.d2;
+      x[3] += o.d3;
+      x[4] += o.d4;
+    }
   }
   {
     // The LI step rests on small changes (Delta y << y in the derivation of
@@ -409,10 +549,17 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
     // step, at most 30 times.  The retry is a trip of the caller's loop, so
     // nothing of this system stays live across it; the system is evaluated
     // again from the same state.
+    // (the FP32 increments: a precise-pass correction is ~1e-7 of them)
     const W e0 = x[0] + dx[0], e1 = x[1] + dx[1], e2 = x[2] + dx[2];
     const bool small = m_abs(e0) <= W(0.5) * fmax_w(S.uf[0], cw.y_floor) &&
                        m_abs(e1) <= W(0.5) * fmax_w(S.uf[1], cw.y_floor) && e2 <= W(1) && e2 >= W(-0.5);
-    if (!small && c.nri < 30) { c.nri++; return false; }
+    if (!small && c.nri < 30 && !(cfg.flags & F_NO_REJECT)) {
+      // rare: counted straight into the statistics (no per-lane registers)
+      if (c.nri == 0) atomicAdd(&stats->rejected, 1ull);
+      atomicAdd(&stats->halvings, 1ull);
+      c.nri++;
+      return false;
+    }
     c.nri = 0;
   }
   double u0[5];
@@ -422,8 +569,8 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
   // abundance increments keep the refinement as a separate FP64 term (they
   // feed y_H = 1 - 2 y_H2 - y_e, which cancels as the gas turns fully
   // molecular or ionized); the relative thermal increments are combined in W.
-  c.u[0] += to_f64(x[0]) + to_f64(dx[0]);
-  c.u[1] += to_f64(x[1]) + to_f64(dx[1]);
+  c.u[0] += inc0;
+  c.u[1] += inc1;
 #pragma unroll
   for (int i = 2; i < 5; ++i) x[i] += dx[i];
   c.u[2] = fma(c.u[2], to_f64(x[2]), c.u[2]);
@@ -498,17 +645,13 @@ __device__ __forceinline__ double y_hminus(double Td, double ye) {
 }
 
 // ------------------------------------------------------------ the kernel
-struct DevStats {
-  unsigned long long cells, substeps, newton, tight, cap, noconv, bad, badstep;
-  unsigned int max_sub, pad;
-};
 
 struct KArgs {
   // state (device pointers)
   const double *nH;
   double *Tg, *Td, *E, *y2, *ye, *yH, *yHp, *yHm;
   uint8_t *status;
-  int32_t *nsub;
+  int32_t *nsub, *niter;
   const double *G0, *nEUV, *NH2;
   // work: flat (ch_start == nullptr) or a chunk table
   int64_t n_cells;
@@ -535,9 +678,9 @@ __device__ __forceinline__ bool nr_attempt(CellRun<double> &c, const DevCfg &cfg
 // of every production call -- all reactions and processes on, no freeze or
 // split flags -- where the mask tests of the rates and the heating and
 // cooling terms fold away at compile time (fewer instructions per substep,
-// a smaller loop for the instruction cache); the refinement choice stays a
-// run-time flag.
-template <typename W, bool MIXED, bool NR = false, bool ALL_ON = false>
+// a smaller loop for the instruction cache); RF fixes the refinement variant
+// at compile time as well (see li_substep).
+template <typename W, bool MIXED, bool NR = false, bool ALL_ON = false, int RF = -1>
 __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -546,7 +689,7 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
   if constexpr (ALL_ON) {
     cfg.rmask = R_ALL;
     cfg.pmask = P_ALL;
-    cfg.flags &= F_REFINE_FF;
+    cfg.flags &= F_REFINE_FF | F_NO_REJECT;
   }
   const CfgW<W> cw = make_cfgw<W>(cfg);
   // warp-uniform chunk cursor
@@ -603,6 +746,7 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
           if (a.yHm) a.yHm[idx] = __longlong_as_double(0x7ff8000000000000LL);
           if (a.status) a.status[idx] = ST_BAD;
           if (a.nsub) a.nsub[idx] = 0;
+          if (a.niter) a.niter[idx] = 0;
         } else {
           make_cellk<W>(c.k, n, G0, nE, NH2, a.cd_factor, cdt, cfg);
           if constexpr (MIXED) project_bits(c.u);
@@ -616,6 +760,7 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
             if (a.yHm) a.yHm[idx] = y_hminus<W>(c.u[2], c.u[1]);
             if (a.status) a.status[idx] = 0;
             if (a.nsub) a.nsub[idx] = 0;
+            if (a.niter) a.niter[idx] = 0;
           }
         }
       }
@@ -626,7 +771,7 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
     if (have) {
       bool done;
       if constexpr (NR) done = nr_attempt(c, cfg, cw);
-      else done = li_substep<W, MIXED>(c, cfg, cw);
+      else done = li_substep<W, MIXED, RF>(c, cfg, cw, a.stats);
       if (done) {
         if constexpr (MIXED && !NR) {
           // the bound y_H2 <= (1 - y_e)/2 not yet applied to the last update
@@ -638,6 +783,7 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
         if (a.yHm) a.yHm[idx] = y_hminus<W>(c.u[2], c.u[1]);
         if (a.status) a.status[idx] = c.st;
         if (a.nsub) a.nsub[idx] = c.nsub;
+        if (a.niter) a.niter[idx] = c.nitr;
         s_sub += (unsigned long long)c.nsub;
         s_newton += (unsigned long long)c.nitr;
         s_max = max(s_max, (unsigned int)c.nsub);

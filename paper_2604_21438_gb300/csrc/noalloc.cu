@@ -7,8 +7,10 @@
 // or in a process that must not grow its device footprint after start-up.
 // sfchem_init allocates the context (counters, statistics, schedule tables),
 // so such callers get this one entry point instead: its scratch lives in a
-// file-scope __device__ array that every GPU holds from the moment the
-// library is loaded until the process exits.
+// file-scope __device__ array.  CUDA loads the library's device code, and
+// with it the array, on a GPU the first time the library uses that GPU (by
+// default lazily, at the first call that needs it), and keeps it until the
+// process exits.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -90,7 +92,8 @@ extern "C" int sfchem_step_batched_noalloc(const sfchem_config_t *cfg, const sfc
     if (!p || !aligned8(p)) return SFCHEM_EINVAL;
   if ((state->y_H && !aligned8(state->y_H)) || (state->y_Hp && !aligned8(state->y_Hp)) ||
       (state->y_Hm && !aligned8(state->y_Hm)) ||
-      (state->n_sub && (reinterpret_cast<uintptr_t>(state->n_sub) & 3u)))
+      (state->n_sub && (reinterpret_cast<uintptr_t>(state->n_sub) & 3u)) ||
+      (state->n_itr && (reinterpret_cast<uintptr_t>(state->n_itr) & 3u)))
     return SFCHEM_EINVAL;
   if (block_offset[0] != 0) return SFCHEM_EINVAL;
   int64_t chunks = 0;
@@ -121,13 +124,16 @@ extern "C" int sfchem_step_batched_noalloc(const sfchem_config_t *cfg, const sfc
     return SFCHEM_ECUDA;
   if (cudaMemcpyAsync(bdt, block_dt, sizeof(double) * n_blocks, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return SFCHEM_ECUDA;
+  // the caller may reuse or free its (possibly pinned) host arrays as soon as
+  // this call returns: wait until the stream has read them
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SFCHEM_ECUDA;
   if (launch_schedule(boff, cost, n_blocks, NA_CHUNK, chs, chc, chb, s) != cudaSuccess) return SFCHEM_ECUDA;
 
   KArgs a;
   std::memset(&a, 0, sizeof(a));
   a.nH = state->n_H; a.Tg = state->T_gas; a.Td = state->T_dust; a.E = state->E_IR;
   a.y2 = state->y_H2; a.ye = state->y_e; a.yH = state->y_H; a.yHp = state->y_Hp; a.yHm = state->y_Hm;
-  a.status = state->status; a.nsub = state->n_sub;
+  a.status = state->status; a.nsub = state->n_sub; a.niter = state->n_itr;
   a.G0 = fields->G0_fuv; a.nEUV = fields->n_euv; a.NH2 = fields->N_H2;
   a.n_cells = block_offset[n_blocks];
   a.chunk = NA_CHUNK;

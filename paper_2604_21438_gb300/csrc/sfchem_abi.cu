@@ -34,7 +34,7 @@ int cuda_fail(cudaError_t e, const char *where) {
   } while (0)
 
 struct GraphKey {
-  const void *ptrs[14];
+  const void *ptrs[15];
   int32_t n_blocks, n_chunks, chunk, tpb, grid;
   double cd_factor;
   sfchem_config_t cfg;
@@ -197,6 +197,7 @@ int check_arrays(const sfchem_state_t *s, const sfchem_fields_t *f) {
   for (const void *p : opt)
     if (p && !aligned(p, 8)) return SFCHEM_EINVAL;
   if (s->n_sub && !aligned(s->n_sub, 4)) return SFCHEM_EINVAL;
+  if (s->n_itr && !aligned(s->n_itr, 4)) return SFCHEM_EINVAL;
   return SFCHEM_OK;
 }
 
@@ -212,7 +213,7 @@ KArgs base_args(sfchem_ctx *ctx, const sfchem_state_t *s, const sfchem_fields_t 
   KArgs a;
   std::memset(&a, 0, sizeof(a));
   a.nH = s->n_H; a.Tg = s->T_gas; a.Td = s->T_dust; a.E = s->E_IR; a.y2 = s->y_H2; a.ye = s->y_e;
-  a.yH = s->y_H; a.yHp = s->y_Hp; a.yHm = s->y_Hm; a.status = s->status; a.nsub = s->n_sub;
+  a.yH = s->y_H; a.yHp = s->y_Hp; a.yHm = s->y_Hm; a.status = s->status; a.nsub = s->n_sub; a.niter = s->n_itr;
   a.G0 = f->G0_fuv; a.nEUV = f->n_euv; a.NH2 = f->N_H2;
   a.cd_factor = cd_factor;
   a.counter = ctx->d_counter;
@@ -250,7 +251,7 @@ int validate_cfg(const sfchem_config_t *c) {
   if (!(std::isfinite(c->gamma_ad) && c->gamma_ad > 1.0)) return SFCHEM_EINVAL;
   if (!(std::isfinite(c->y_floor) && c->y_floor > 0.0)) return SFCHEM_EINVAL;
   if (!(std::isfinite(c->nr_tol) && c->nr_tol > 0.0)) return SFCHEM_EINVAL;
-  if (c->reaction_mask >> 12 || c->process_mask >> 17 || c->flags >> 7 || c->reserved) return SFCHEM_EINVAL;
+  if (c->reaction_mask >> 12 || c->process_mask >> 17 || c->flags >> 8 || c->reserved) return SFCHEM_EINVAL;
   return SFCHEM_OK;
 }
 
@@ -346,7 +347,8 @@ int batched_launch(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_fi
   if (!use_graph) return record_batched(ctx, a, sh, n_blocks, s);
   GraphKey k;
   std::memset(&k, 0, sizeof(k));
-  const void *p[14] = {a.nH, a.Tg, a.Td, a.E, a.y2, a.ye, a.yH, a.yHp, a.yHm, a.status, a.nsub, a.G0, a.nEUV, a.NH2};
+  const void *p[15] = {a.nH, a.Tg, a.Td, a.E, a.y2, a.ye, a.yH, a.yHp, a.yHm, a.status, a.nsub, a.niter,
+                       a.G0, a.nEUV, a.NH2};
   std::memcpy(k.ptrs, p, sizeof(p));
   k.n_blocks = n_blocks; k.n_chunks = a.n_chunks; k.chunk = sh.chunk; k.tpb = sh.tpb; k.grid = sh.grid;
   k.cd_factor = cd_factor; k.cfg = ctx->cfg; k.sched_version = ctx->sched_version;
@@ -635,6 +637,7 @@ int sfchem_step_host(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_
     st.y_Hm = state->y_Hm ? f[11] : nullptr;
     st.status = state->status ? ctx->stage_status[k] : nullptr;
     st.n_sub = state->n_sub ? ctx->stage_nsub[k] : nullptr;
+    st.n_itr = nullptr;   // not staged: sfchem_step_host does not write n_itr
     sfchem_fields_t fl;
     fl.G0_fuv = f[6]; fl.n_euv = f[7]; fl.N_H2 = f[8];
     KArgs a = base_args(ctx, &st, &fl, cd_factor);
@@ -772,6 +775,72 @@ int sfchem_autotune(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_f
   return SFCHEM_OK;
 }
 
+// Greedy test of a bottleneck: can blocks [0, n) be cut into at most
+// n_parts contiguous ranges whose costs stay <= cap?  Writes the cut when
+// `cut` is not NULL (ranges left over at the end are empty).
+static bool partition_fits(const double *cost, int32_t n, int32_t n_parts, double cap, int32_t *cut) {
+  int32_t part = 0;
+  double acc = 0.0;
+  if (cut) cut[0] = 0;
+  for (int32_t b = 0; b < n; ++b) {
+    if (acc > 0.0 && acc + cost[b] > cap) {
+      if (++part >= n_parts) return false;
+      if (cut) cut[part] = b;
+      acc = 0.0;
+    }
+    acc += cost[b];
+  }
+  if (cut)
+    for (int32_t k = part + 1; k <= n_parts; ++k) cut[k] = n;
+  return true;
+}
+
+int sfchem_partition(const int64_t *block_offset, const double *block_cost, int32_t n_blocks, int32_t n_parts,
+                     int32_t *cut) {
+  if (!block_offset || !cut || n_blocks < 0 || n_parts < 1) return SFCHEM_EINVAL;
+  if (block_offset[0] != 0) return SFCHEM_EINVAL;
+  std::vector<double> cost(n_blocks);
+  double total = 0.0, big = 0.0;
+  for (int32_t b = 0; b < n_blocks; ++b) {
+    const int64_t cells = block_offset[b + 1] - block_offset[b];
+    if (cells < 0) return SFCHEM_EINVAL;
+    double c = block_cost ? block_cost[b] : (double)cells;
+    if (!(std::isfinite(c) && c >= 0.0)) return SFCHEM_EINVAL;
+    // a block that costs nothing measurable still takes time to load and store
+    if (block_cost && c == 0.0) c = (double)cells;
+    cost[b] = c;
+    total += c;
+    big = std::max(big, c);
+  }
+  if (n_blocks == 0 || total == 0.0) {
+    for (int32_t k = 0; k <= n_parts; ++k) cut[k] = k == 0 ? 0 : n_blocks;
+    return SFCHEM_OK;
+  }
+  // bisection on the largest part cost between its lower bound
+  // max(total / n_parts, largest block) and the greedy bound lo + largest
+  // block, to a relative width of 1e-12
+  double lo = std::max(total / n_parts, big), hi = lo + big;
+  while (!partition_fits(cost.data(), n_blocks, n_parts, hi, nullptr)) hi *= 2.0;   // rounding safety
+  for (int it = 0; it < 200 && hi - lo > 1e-12 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (partition_fits(cost.data(), n_blocks, n_parts, mid, nullptr)) hi = mid;
+    else lo = mid;
+  }
+  partition_fits(cost.data(), n_blocks, n_parts, hi, cut);
+  return SFCHEM_OK;
+}
+
+int sfchem_block_costs(sfchem_ctx *ctx, float *cost, int32_t n_blocks) {
+  if (int rc = check_ctx(ctx)) return rc;
+  if (!cost || n_blocks < 0 || n_blocks > ctx->cap_blocks ||
+      (int64_t)ctx->h_block_dt.size() != n_blocks)
+    return SFCHEM_EINVAL;
+  if (n_blocks == 0) return SFCHEM_OK;
+  SFC_CUDA(cudaDeviceSynchronize());
+  SFC_CUDA(cudaMemcpy(cost, ctx->d_block_cost, sizeof(float) * n_blocks, cudaMemcpyDeviceToHost));
+  return SFCHEM_OK;
+}
+
 int sfchem_stats(sfchem_ctx *ctx, sfchem_stats_t *out) {
   if (int rc = check_ctx(ctx)) return rc;
   if (!out) return SFCHEM_EINVAL;
@@ -788,6 +857,8 @@ int sfchem_stats(sfchem_ctx *ctx, sfchem_stats_t *out) {
   out->noconv_cells = d.noconv;
   out->badinput_cells = d.bad;
   out->badstep_cells = d.badstep;
+  out->rejected_substeps = d.rejected;
+  out->step_halvings = d.halvings;
   out->max_substeps = d.max_sub;
   float ms = 0.0f;
   if (ctx->timed && cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) out->last_kernel_ms = ms;
