@@ -34,17 +34,19 @@ import inputs  # noqa: E402
 METRIC = "chem+thermal cell-updates/s: mixed/batched vs plain FP64 at stated error"
 YR = inputs.YR
 
-# Algorithmic work per cell-substep of the solver kernels: the FP
+# Executed FP work per cell-substep of the solver kernels: the FP
 # instructions that ncu counts per launch (FMA = 2 flops, add/mul = 1),
-# divided by the substeps of that launch (GRF 128^3 workload, dt = 1e3 yr,
-# C_d = 1e4); profiles/sfchem_li_{mixed,fp64}_grf128.md.
+# divided by the substeps of that launch, on the first 512 blocks of the
+# GMC-like 256^3 workload (2,097,152 cells, dt = 1e3 yr, C_d = 1e6);
+# profiles/sfchem_li_mixed_gmc256.md, profiles/sfchem_li_fp64_gmc256.md.
+PROFILE_SOURCE = "ncu capture of the GMC-like 256^3 workload, first 512 blocks (profiles/)"
 WORK_PER_SUBSTEP = {
-    "mixed": {"fp32_flops": 1291.5, "fp64_flops": 48.0},
+    "mixed": {"fp32_flops": 1396.4, "fp64_flops": 30.2},
     "fp64": {"fp32_flops": 7.5, "fp64_flops": 2003.8},
 }
-# DRAM bytes per cell of one solver launch (same captures: 269.3 MB for
-# 2,097,152 cells, mixed; 274.6 MB, FP64).
-DRAM_BYTES_PER_CELL = {"mixed": 269.35e6 / 2097152, "fp64": 274.61e6 / 2097152}
+# DRAM bytes per cell of one solver launch (same captures: 290.9 MB for
+# 2,097,152 cells, mixed).
+DRAM_BYTES_PER_CELL = {"mixed": 290.91e6 / 2097152, "fp64": 274.61e6 / 2097152}
 # GB300 ALU peaks from unit counts and the SM clock: 152 SMs; FP32 128
 # lanes/SM (256 flops/clk); FP64 2 DFMA/clk/SM (4 flops/clk) -- the
 # "peak_sustained" of the FP64 pipe that ncu reports, 1.26 TFLOP/s at 2.07 GHz.
@@ -73,6 +75,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (error check, cpu_baseline)")
     p.add_argument("--sample", type=int, default=4096, help="cells checked against the oracle")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the cpu_baseline")
+    p.add_argument("--slice-blocks", type=int, default=0,
+                   help="use only the first N blocks of the workload (small cases for profiling)")
+    p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg through host buffers")
     return p.parse_args()
 
 
@@ -197,7 +202,15 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    cells, off, bdt, cd, desc = make_workload(args.workload, rank, args.Z)
+    if world > 1 and args.workload == "gmc256":
+        cells, off, bdt, cd, desc = sharded_gmc(args, rank, world, dev)
+    else:
+        cells, off, bdt, cd, desc = make_workload(args.workload, rank, args.Z)
+    if args.slice_blocks:
+        nb = min(args.slice_blocks, len(bdt))
+        cells = inputs.subset(cells, np.arange(int(off[nb])))
+        off, bdt = off[:nb + 1], bdt[:nb]
+        desc = dict(desc, cells=int(off[-1]), blocks=nb, slice=f"first {nb} blocks")
     Z = desc.get("Z", 1.0)
     n = len(cells["n_H"])
     stream = torch.cuda.current_stream()
@@ -245,6 +258,20 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     out_m = sf.to_host({k: d[k] for k in sf.STATE_FIELDS + ("status", "n_sub")})
     res["mixed"] = dict(ms=ms_m, wall=wall_m, stats=st_m, launch=sm.get_launch())
+    # ---- photon consumption after the update (sfchem_photon_update), on the
+    # updated state; HBM-bound: 6 FP64 reads and 2 FP64 writes per cell
+    g_out, e_out = torch.empty_like(d["G0"]), torch.empty_like(d["n_EUV"])
+    for _ in range(3):
+        sf.photon_update(d, float(bdt[0]), G0_out=g_out, n_euv_out=e_out)
+    torch.cuda.synchronize()
+    pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+    for a0, b0 in pe:
+        a0.record(stream)
+        sf.photon_update(d, float(bdt[0]), G0_out=g_out, n_euv_out=e_out)
+        b0.record(stream)
+    torch.cuda.synchronize()
+    res["photon"] = dict(ms=float(np.mean([a0.elapsed_time(b0) for a0, b0 in pe])))
+    del g_out, e_out
     # ---- mixed precision with the error-free FP32 refinement residual
     out_ff = None
     if not args.no_ff:
@@ -287,6 +314,11 @@ def run_ours(args, rank, world, local_rank):
     # ---- end to end through the public API with host buffers: sfchem_step_host
     # copies each slice's inputs in and its results out on two streams while
     # the previous slice is solved; the state is reset outside the timed region
+    if args.no_e2e:
+        e2e_ms = float("nan")
+        sm.close()
+        return finish_line(args, rank, world, res, clk, n, cells, off, bdt, cd, desc, Z, ms_m, e2e_ms, out_m,
+                           out_d, out_ff, 0, 0)
     pristine_h = {k: torch.as_tensor(cells[k]).pin_memory() for k in sf.STATE_FIELDS}
     host = {k: torch.as_tensor(cells[k]).pin_memory() for k in sf.STATE_FIELDS + sf.INPUT_FIELDS}
     host["status"] = torch.empty(n, dtype=torch.uint8).pin_memory()
@@ -307,11 +339,17 @@ def run_ours(args, rank, world, local_rank):
             e2e_times.append(a.elapsed_time(b))
     e2e_ms = float(np.mean(e2e_times))
     sm.close()
+    return finish_line(args, rank, world, res, clk, n, cells, off, bdt, cd, desc, Z, ms_m, e2e_ms, out_m, out_d,
+                       out_ff, h2d, d2h)
 
+
+def finish_line(args, rank, world, res, clk, n, cells, off, bdt, cd, desc, Z, ms_m, e2e_ms, out_m, out_d, out_ff,
+                h2d, d2h):
+    """The JSON line of our arm from the legs' measurements."""
     # cross-rank aggregation: max time over ranks
     ms_m_max = allreduce_max(ms_m, world)
     e2e_max = allreduce_max(e2e_ms, world)
-    total_cells = n * world
+    total_cells = int(round(allreduce_sum(float(n), world)))
     value = total_cells / (ms_m_max * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
@@ -319,13 +357,25 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
         "config": dict(desc, precision="mixed", path="sfchem_step_batched (persistent kernel, CUDA graph)",
                        l2="inputs (2.4 GB) larger than L2; state reset from a device copy before each step",
-                       parallelism=f"independent cell shards x{world}"),
-        "e2e": {"value": total_cells / (e2e_max * 1e-3), "unit": "cell-updates/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max,
-                "path": "sfchem_step_host: pinned host state, copies overlapped with the solver slice by slice"},
+                       parallelism=(f"one workload in {world} cost-balanced block ranges (no data-path collective)"
+                                    if world > 1 else "one device")),
+        "e2e": None if not np.isfinite(e2e_max) else {
+            "value": total_cells / (e2e_max * 1e-3), "unit": "cell-updates/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max,
+            "path": "sfchem_step_host: pinned host state, copies overlapped with the solver slice by slice"},
         "gpu_launches": 2 * args.steps,   # per step: schedule kernel + persistent solver kernel
         "clocks": clk,
     }
+    if "photon" in res:
+        peaks, src = measured_peaks()
+        ms_p = res["photon"]["ms"]
+        gbs = 64.0 * n / (ms_p * 1e-3) / 1e9
+        line["photon_update"] = {
+            "kernel": "sfchem_photon_kernel", "ms": ms_p, "cells": n,
+            "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": peaks["hbm_gbs"],
+                         "frac": gbs / peaks["hbm_gbs"], "peak_source": src,
+                         "bytes_per_cell": 64, "traffic": None},
+            "note": "photon consumption after the update (reading of Sec. 2.2.8), timed alone over 10 launches"}
     if "mixed_ff" in res:
         ms_f_max = allreduce_max(res["mixed_ff"]["ms"], world)
         line["mixed_ff"] = {"value": total_cells / (ms_f_max * 1e-3), "ms_per_step": ms_f_max,
@@ -346,6 +396,9 @@ def run_ours(args, rank, world, local_rank):
         line["speedup_mixed_vs_fp64"] = ms_d_max / ms_m_max
     st = res["mixed"]["stats"]
     line["substeps_per_cell"] = st["substeps"] / max(st["cells"], 1)
+    line["step_rejection"] = {"rejected_substeps": st["rejected_substeps"], "step_halvings": st["step_halvings"],
+                              "fraction_of_substeps": st["rejected_substeps"] / max(st["substeps"], 1),
+                              "note": "substeps redone by the step-rejection reading (mixed leg, all timed steps)"}
     line["tight_fraction"] = st["tight_cells"] / max(st["cells"], 1)
     line["launch"] = res["mixed"]["launch"]
     try:
@@ -353,21 +406,40 @@ def run_ours(args, rank, world, local_rank):
     except Exception as exc:  # the measurement is informational
         line["alu_peaks_microbench_tflops"] = {"error": str(exc)}
     # roofline of the dominant kernel (the mixed solver kernel)
-    line["roofline"] = roofline(res, clk, n, "mixed")
+    alg = None
+    if rank == 0 and not args.no_cpu:
+        try:
+            alg = algorithmic_work(cells, off, bdt, cd, Z=Z)
+        except Exception as exc:  # informational
+            alg = None
+            line["algorithmic_work_error"] = str(exc)
+    line["roofline"] = roofline(res, clk, n, "mixed", alg)
     if "fp64" in res:
-        line["roofline_fp64"] = roofline(res, clk, n, "fp64")
+        line["roofline_fp64"] = roofline(res, clk, n, "fp64", alg)
+    if alg is not None:
+        line["algorithmic_work"] = alg
     if rank == 0 and not args.no_cpu:
         line["error_vs_oracle"] = error_vs_oracle(cells, off, bdt, cd, out_m, out_d, args.sample, out_ff, Z=Z)
         line["cpu_baseline"] = cpu_baseline(cells, off, bdt, cd, args.cpu_seconds, Z=Z)
     return line
 
 
-def roofline(res, clk, n_cells, leg="mixed"):
-    """ALU roofline of a solver kernel: algorithmic FP work per cell-substep
-    (WORK_PER_SUBSTEP) x substeps of one launch / its CUDA-event time.  The
-    reported pipe is the one closest to its peak (FP64 for both kernels:
-    on GB300 the FP64 rate is 1/64 of FP32); the other pipe's fraction is
-    given beside it."""
+def roofline(res, clk, n_cells, leg="mixed", alg=None):
+    """ALU roofline of a solver kernel.
+
+    Primary (achieved / peak / frac): the method's algorithmic work -- the
+    oracle's op count W per substep on a sample of this workload
+    (algorithmic_work) x the substeps of one launch -- over the launch's
+    CUDA-event time, against the peak of the precision the kernel computes
+    the method in: FP32 for the mixed kernel, FP64 for the plain one (unit
+    counts x max SM clock).  W counts the oracle's dual-number Jacobian and
+    its two double-word refinements, about twice what the kernels execute,
+    so the plain FP64 kernel can read above 1.0.
+
+    kernel_counted: the FP instructions the kernel executes per substep
+    (WORK_PER_SUBSTEP, from the ncu capture of the GMC-like slice) on the
+    pipe that binds it (FP64 for both kernels: on GB300 the FP64 rate is
+    1/64 of FP32), with the other pipe beside it."""
     st = res[leg]["stats"]
     subs = st["substeps"] / max(st["calls"], 1)
     ms = res[leg]["ms"]
@@ -377,16 +449,29 @@ def roofline(res, clk, n_cells, leg="mixed"):
     peak32 = N_SM * FP32_FLOP_PER_SM_CLK * f_mhz * 1e6 / 1e12
     a64 = w["fp64_flops"] * subs / (ms * 1e-3) / 1e12
     a32 = w["fp32_flops"] * subs / (ms * 1e-3) / 1e12
-    out = {"bound": "alu", "unit": "TFLOP/s", "kernel": f"sfchem_li_{leg}",
-           "substeps_per_launch": subs, "kernel_ms": ms,
-           "traffic": DRAM_BYTES_PER_CELL[leg] * n_cells,
-           "traffic_note": "dram bytes of one launch, scaled by cells from the GRF 128^3 capture"}
+    kc = {"flops_per_substep": w, "source": PROFILE_SOURCE}
     if a64 / peak64 >= a32 / peak32:
-        out.update(achieved=a64, peak=peak64, frac=a64 / peak64, pipe="fp64",
-                   other={"pipe": "fp32", "achieved": a32, "peak": peak32, "frac": a32 / peak32})
+        kc.update(pipe="fp64", achieved=a64, peak=peak64, frac=a64 / peak64,
+                  other={"pipe": "fp32", "achieved": a32, "peak": peak32, "frac": a32 / peak32})
     else:
-        out.update(achieved=a32, peak=peak32, frac=a32 / peak32, pipe="fp32",
-                   other={"pipe": "fp64", "achieved": a64, "peak": peak64, "frac": a64 / peak64})
+        kc.update(pipe="fp32", achieved=a32, peak=peak32, frac=a32 / peak32,
+                  other={"pipe": "fp64", "achieved": a64, "peak": peak64, "frac": a64 / peak64})
+    out = {"bound": "alu", "unit": "TFLOP/s", "kernel": f"sfchem_li_{leg}", "substeps_per_launch": subs,
+           "kernel_ms": ms, "traffic": DRAM_BYTES_PER_CELL[leg] * n_cells,
+           "traffic_note": "dram bytes of one launch: bytes per cell of the ncu capture x cells",
+           "algorithmic_bytes": 141 * n_cells}
+    peak = peak32 if leg == "mixed" else peak64
+    if alg is not None:
+        aw = alg["flops_per_substep"] * subs / (ms * 1e-3) / 1e12
+        out.update(achieved=aw, peak=peak, frac=aw / peak, pipe="fp32" if leg == "mixed" else "fp64",
+                   work="algorithmic: oracle op count W per substep x substeps of the launch",
+                   W_flops_per_substep=alg["flops_per_substep"],
+                   W_transcendentals_per_substep=alg["transcendentals_per_substep"])
+    else:
+        # without the oracle (--no-cpu) only the executed-instruction view exists
+        out.update(achieved=kc["achieved"], peak=kc["peak"], frac=kc["frac"], pipe=kc["pipe"],
+                   work="kernel-counted (no oracle op count in this run)")
+    out["kernel_counted"] = kc
     out["peak_source"] = "unit counts x max SM clock (recipe); FMA microbenchmark in alu_peaks_microbench_tflops"
     return out
 
@@ -411,14 +496,20 @@ def error_vs_oracle(cells, off, bdt, cd, out_m, out_d, sample, out_ff=None, Z=1.
         if got is None:
             continue
         res = {}
-        for k in ("T_g", "T_d", "E_IR", "y_H2", "y_e"):
-            a, b = got[k][idx], ref[k]
-            floor = 1e-6 if k.startswith("y_") else 1e-300
-            e = np.abs(a - b) / np.maximum(np.abs(b), floor)
-            res[k] = {"max": float(e.max()), "p99": float(np.percentile(e, 99)), "median": float(np.median(e))}
+        got_yH = 1.0 - 2.0 * got["y_H2"][idx] - got["y_e"][idx]
+        for k in ("T_g", "T_d", "E_IR", "y_H2", "y_e", "y_H"):
+            a = got_yH if k == "y_H" else got[k][idx]
+            b = ref[k]
+            big = np.abs(b) > 1e-8
+            d = np.abs(a - b)
+            e = d[big] / np.abs(b[big])
+            res[k] = {"max": float(e.max()) if e.size else 0.0,
+                      "p99": float(np.percentile(e, 99)) if e.size else 0.0,
+                      "median": float(np.median(e)) if e.size else 0.0,
+                      "abs_max_below_1e-8": float(d[~big].max()) if (~big).any() else 0.0}
         res["n_sub_mismatch"] = int((got["n_sub"][idx] != ref["n_sub"]).sum())
         out[name] = res
-    out["metric"] = "relative error; abundances below 1e-6 in units of 1e-6"
+    out["metric"] = "relative error where the oracle's value exceeds 1e-8, absolute error below"
     return out
 
 
@@ -439,8 +530,35 @@ def cpu_baseline(cells, off, bdt, cd, target_s, Z=1.0):
             break
         m = int(min(n, max(2 * m, m * 0.6 * target_s / max(dt, 1e-3))))
     cores = os.cpu_count()
-    return {"value": idx.size / dt, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
-            "sample": f"{idx.size} seeded cells of the workload, one step, {dt:.1f} s wall on {cores} threads"}
+    out = {"value": idx.size / dt, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+           "sample": f"{idx.size} seeded cells of the workload, one step, {dt:.1f} s wall on {cores} threads"}
+    # the same oracle on one host thread, on a quarter of that sample
+    q = idx[: max(64, idx.size // max(4, cores // 4))]
+    blk = np.searchsorted(off, q, side="right") - 1
+    t0 = time.perf_counter()
+    oracle.li_step(inputs.subset(cells, q), bdt[blk], cd, oracle_config(Z), n_threads=1)
+    d1 = time.perf_counter() - t0
+    out["single_thread"] = {"value": q.size / d1, "unit": "cell-updates/s", "cores": 1,
+                            "sample": f"{q.size} cells of the same sample, {d1:.1f} s wall on 1 thread"}
+    return out
+
+
+def algorithmic_work(cells, off, bdt, cd, Z=1.0, sample=256):
+    """Floating-point work of the method per substep, counted by running the
+    oracle's LI step with an op-counting scalar type on a seeded sample of
+    the workload (flops: add, mul, div = 1, fma = 2; transcendentals apart)."""
+    import oracle
+    n = len(cells["n_H"])
+    idx = np.sort(np.random.default_rng(31).choice(n, min(sample, n), replace=False))
+    blk = np.searchsorted(off, idx, side="right") - 1
+    r = oracle.opcount(inputs.subset(cells, idx), bdt[blk], cd, oracle_config(Z))
+    per = r["per_substep"]
+    sec = {k: sum(v[o] * (2 if o == "fma" else 1) for o in ("add", "mul", "div", "fma")) / max(r["substeps"], 1)
+           for k, v in r["counts"].items()}
+    return {"flops_per_substep": per["flops"], "transcendentals_per_substep": per["transcendentals"],
+            "by_section_flops_per_substep": sec, "sample_cells": int(idx.size), "sample_substeps": r["substeps"],
+            "how": "oracle LI step with an op-counting scalar type (oracle/opcount.cpp): forward-mode dual-number "
+                   "Jacobian, equilibrated dense 5x5 elimination with two double-word refinements"}
 
 
 # ------------------------------------------------------------ reference arm
@@ -509,6 +627,17 @@ def barrier(world):
         dist.barrier()
 
 
+def allreduce_sum(x: float, world: int) -> float:
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def allreduce_max(x: float, world: int) -> float:
     if world <= 1:
         return float(x)
@@ -518,6 +647,87 @@ def allreduce_max(x: float, world: int) -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def shard_slabs(cut, rank: int, slab_blocks: int):
+    """The pieces of rank `rank`'s contiguous block range [cut[rank],
+    cut[rank + 1]) of a workload made of equal slabs of slab_blocks blocks:
+    a list of (slab, first block, end block) with block indices local to the
+    slab, in order."""
+    lo, hi = int(cut[rank]), int(cut[rank + 1])
+    out = []
+    b = lo
+    while b < hi:
+        s = b // slab_blocks
+        e = min(hi, (s + 1) * slab_blocks)
+        out.append((s, b - s * slab_blocks, e - s * slab_blocks))
+        b = e
+    return out
+
+
+def sharded_gmc(args, rank: int, world: int, dev):
+    """One workload of `world` GMC-like 256^3 slabs (seeds 1005 + slab), split
+    into contiguous block ranges balanced by cost (Sec. 4: the
+    thermochemical update runs independently on each device).  Each rank
+    first advances its own slab once (untimed) to measure its per-block
+    substeps; the costs are gathered, sfchem_partition cuts the block list,
+    and each rank assembles its range (whole blocks, from at most a few
+    slabs)."""
+    import paper_2604_21438_gb300 as sf
+    import torch
+    slab = {}
+
+    def get(sidx):
+        if sidx not in slab:
+            c = inputs.cells_gmc(256, seed=1005 + sidx)
+            slab[sidx] = inputs.block_major(c, 256, 16)
+        return slab[sidx]
+
+    own, off = get(rank)
+    nb = len(off) - 1
+    bdt = np.full(nb, 1e3 * YR)
+    s = sf.Solver("mixed")
+    d = sf.to_device(own, dev, outputs=False)
+    s.step_batched(d, off, bdt, 100.0)
+    torch.cuda.synchronize()
+    cost = gather_block_costs(s.block_costs(nb).astype(np.float64), rank * nb, world * nb, world)
+    s.close()
+    del d
+    off_g = np.concatenate([[0], np.cumsum(np.tile(np.diff(off), world))]).astype(np.int64)
+    cut = sf.partition(off_g, world, cost)
+    parts = []
+    offs = [0]
+    for sidx, b0, b1 in shard_slabs(cut, rank, nb):
+        c, o = get(sidx)
+        parts.append(inputs.subset(c, np.arange(int(o[b0]), int(o[b1]))))
+        offs.extend((offs[-1] + np.diff(o[b0:b1 + 1])).tolist())
+    for k in [k for k in slab if k != rank]:
+        del slab[k]
+    cells = inputs.concat(*parts)
+    loads = [float(cost[cut[r]:cut[r + 1]].sum()) for r in range(world)]
+    off_r = np.array(offs, np.int64)
+    desc = dict(workload=f"GMC-like 256^3 grid x {world} slabs (one workload) in 16^3 blocks, cost-balanced "
+                         f"contiguous block ranges per rank",
+                cells=int(off_r[-1]), dt_yr=1e3, cd_factor=100.0, blocks=len(off_r) - 1, block_cells=4096,
+                partition={"cut": [int(x) for x in cut], "cost": "substeps per block of a warm-up call",
+                           "load_max_over_mean": max(loads) / (sum(loads) / world)})
+    return cells, off_r, np.full(len(off_r) - 1, 1e3 * YR), 100.0, desc
+
+
+def gather_block_costs(mine, lo: int, n_blocks: int, world: int):
+    """The per-block costs of one workload, from each rank's costs of its own
+    block range [lo, lo + len(mine)): a sum-reduction of zero-padded vectors
+    (a host-side exchange between steps, not part of the timed step)."""
+    full = np.zeros(n_blocks, np.float64)
+    full[lo:lo + len(mine)] = mine
+    if world <= 1:
+        return full
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.as_tensor(full, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t.cpu().numpy()
 
 
 def run_sweep(args):

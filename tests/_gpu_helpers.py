@@ -5,24 +5,48 @@ import numpy as np
 import inputs
 
 FIELDS_CMP = ("T_g", "T_d", "E_IR", "y_H2", "y_e", "y_H")
-# An abundance carries an absolute rounding error of about eps times the
-# largest value it held along the trajectory (up to 1), so relative errors are
-# taken only above 1e-6; below, the error is measured in units of 1e-6
-# (1e-9 of relative error at the threshold = 1e-15 absolute).
-Y_FLOOR = 1e-6
+
+# The FP64 bar (the thresholds of the mixed-precision workload description:
+# relative above 1e-8, absolute below): 1e-9 relative on T_g, T_d, E_IR and
+# on abundances above 1e-8, 1e-17 absolute below.  y_H = 1 - 2 y_H2 - y_e is
+# formed by subtraction from 1, so its absolute rounding is that of numbers
+# near 1: its bar is max(1e-9 |y_H|, 2^-52).
+Y_SMALL = 1e-8
+FP64_REL, FP64_ABS, ULP1 = 1e-9, 1e-17, 2.0 ** -52
 
 
-def cell_errors(got, ref, idx=None, y_floor=Y_FLOOR):
-    """Per cell, the largest normalised error over FIELDS_CMP."""
+def fp64_score(got, ref, idx=None):
+    """Per cell, the largest error over FIELDS_CMP in units of its FP64 bar
+    (a cell meets the bar when the score is <= 1)."""
     worst = None
     for k in FIELDS_CMP:
         a, b = got[k], ref[k]
         if idx is not None:
             a = a[idx]
-        floor = y_floor if k.startswith("y_") else 1e-300
-        e = np.abs(a - b) / np.maximum(np.abs(b), floor)
+        d = np.abs(a - b)
+        if k == "y_H":
+            bar = np.maximum(FP64_REL * np.abs(b), ULP1)
+        elif k.startswith("y_"):
+            bar = np.where(np.abs(b) > Y_SMALL, FP64_REL * np.abs(b), FP64_ABS)
+        else:
+            bar = FP64_REL * np.abs(b)
+        e = d / bar
         worst = e if worst is None else np.maximum(worst, e)
     return worst
+
+
+def mixed_errors(got, ref, idx=None):
+    """Per field, per cell: the relative error where |ref| > 1e-8 (NaN below)
+    and the absolute error where |ref| <= 1e-8 (NaN above)."""
+    out = {}
+    for k in FIELDS_CMP:
+        a, b = got[k], ref[k]
+        if idx is not None:
+            a = a[idx]
+        big = np.abs(b) > Y_SMALL
+        d = np.abs(a - b)
+        out[k] = (np.where(big, d / np.where(big, np.abs(b), 1.0), np.nan), np.where(big, np.nan, d))
+    return out
 
 
 def run_gpu(cells, dt, cd_factor=1.0, precision="fp64", batched=None, **cfg):

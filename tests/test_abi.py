@@ -35,7 +35,7 @@ def test_default_config_and_validation():
     assert c.reaction_mask == 0xFFF and c.process_mask == sf.P_ALL and c.flags == 0
     assert L.sfchem_config_validate(ctypes.byref(c)) == sf.OK
     bad = [dict(f_chem=0.0), dict(f_chem=1.5), dict(n_cyc=0), dict(gamma_ad=1.0), dict(y_floor=0.0),
-           dict(precision=2), dict(reaction_mask=1 << 12), dict(process_mask=1 << 17), dict(flags=1 << 7),
+           dict(precision=2), dict(reaction_mask=1 << 12), dict(process_mask=1 << 17), dict(flags=1 << 8),
            dict(nr_tol=-1.0), dict(Z=float("nan")), dict(reserved=1), dict(n_sub_max=0)]
     for kw in bad:
         c = sf.default_config(**kw)

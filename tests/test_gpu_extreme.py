@@ -10,7 +10,7 @@ import pytest
 
 import inputs
 import oracle
-from _gpu_helpers import cell_errors, run_gpu
+from _gpu_helpers import fp64_score, run_gpu
 
 pytestmark = pytest.mark.gpu
 TCMB = 2.725
@@ -33,7 +33,7 @@ def test_extreme_cells(dt_yr):
     m = run_gpu(cells, dt_yr * inputs.YR, 100.0, precision="mixed")
     _physical(d)
     _physical(m)
-    e = cell_errors(d, ref)
-    print(dt_yr, "fp64 within 1e-9: %.3f, median %.1e" % ((e <= 1e-9).mean(), np.median(e)))
-    assert np.median(e) <= 1e-9
+    e = fp64_score(d, ref)
+    print(dt_yr, "fp64 within the bar: %.3f, median score %.1e" % ((e <= 1.0).mean(), np.median(e)))
+    assert np.median(e) <= 1.0
     assert np.all(d["status"] & 2 == ref["status"] & 2) and np.all(m["status"] & 2 == ref["status"] & 2)

@@ -1,64 +1,70 @@
 """FP64 CUDA path against the CPU oracle, element by element (same seeded
 inputs).
 
-Bar: 1e-9 relative on temperatures, E_IR and abundances above 1e-6 (1e-15
-absolute below) and identical substep counts and status bits, in at least
-99.5 per cent of the cells.  The few cells allowed past 1e-9 are cells whose
-substep size is set by Eq. timescale_energy close to thermal balance: there
-|Gamma - Lambda| is a small difference of large terms, so rounding
-differences of 1e-16 between two FP64 evaluations of the rates are amplified
-in dt_energy and carried into later substeps.  The oracle's own result
-carries the same sensitivity, and the test checks that it does: every cell
-past 1e-6 must be one whose oracle result moves by more than 1e-9 when one
-input changes by one ulp (GRF 128^3, dt = 1e4 yr, C_d = 1e7: a handful of
-65,536 cells, up to 3e-3 after ~550 substeps); every cell stays within
-1e-2."""
+Bar, per cell: 1e-9 relative on T_g, T_d, E_IR and on abundances above 1e-8,
+1e-17 absolute below (y_H, formed by subtraction from 1: max(1e-9 |y_H|,
+2^-52)), identical substep count and identical status bits.  A cell may miss
+it only in proportion to how much the oracle's own result depends on FP64
+rounding: by at most 1e3 times the largest change of the oracle's result
+when (a) one input (T_g, y_H2 or n_H) moves by one ulp, (b) the oracle is
+compiled with floating-point contraction (another valid FP64 rounding
+sequence; on the aarch64 host of the GPU the two differ), or (c) every
+entry of each substep's linear system moves by 1e-15 of itself (about 4
+ulp: the CUDA path forms the same systems from other formulas -- relative
+unknowns, a hand-derived Jacobian, CUDA's exp and log -- which differ from
+the oracle's entries by a few ulp).  Measured: such cells occur only where
+the substep is set by Eq. timescale_energy close to thermal balance, where
+|Gamma - Lambda| is a small difference of large terms and rounding-level
+changes move dt_energy and the substep sequence (GRF 128^3, dt = 1e4 yr,
+C_d = 1e7: a few dozen of 65,536 cells, up to 1e-4 after ~500 substeps);
+every other sample meets the bar in every cell."""
 import numpy as np
 import pytest
 
 import inputs
 import oracle
-from _gpu_helpers import cell_errors, run_gpu, sample_with_flagged
+from _gpu_helpers import fp64_score, run_gpu, sample_with_flagged
 
 pytestmark = pytest.mark.gpu
 YR = inputs.YR
-RTOL = 1e-9
-FRAC_OK = 0.995
-HARD = 1e-2        # every cell
-SENSITIVE = 1e-6   # cells past this must be ill-conditioned in the oracle itself
+AMPLIFICATION = 1e3   # largest error / one-ulp oracle sensitivity allowed past the bar
 
 
-def oracle_ulp_sensitivity(cell, dt, cd, cfg=None):
-    """Largest change of the oracle's result when one of T_g, y_H2, n_H moves
-    by one ulp."""
+def oracle_rounding_sensitivity(cell, dt, cd, cfg=None):
+    """How much the oracle's own result depends on FP64 rounding, in units of
+    the FP64 bar: the largest change when one of T_g, y_H2, n_H moves by one
+    ulp, when the oracle is evaluated with contraction (fma=True), or when
+    every entry of its substep systems moves by +-1e-15 of itself."""
     one = {k: np.array([float(v)]) for k, v in cell.items()}
     r0 = oracle.li_step(one, dt, cd, cfg)
-    out = 0.0
+    out = float(fp64_score(oracle.li_step(one, dt, cd, cfg, fma=True), r0).max())
+    for eps in (1e-15, -1e-15):
+        out = max(out, float(fp64_score(oracle.li_step(one, dt, cd, cfg, perturb=eps), r0).max()))
     for k in ("T_g", "y_H2", "n_H"):
         p = dict(one)
         p[k] = np.nextafter(one[k], np.inf)
-        out = max(out, float(cell_errors(oracle.li_step(p, dt, cd, cfg), r0).max()))
+        out = max(out, float(fp64_score(oracle.li_step(p, dt, cd, cfg), r0).max()))
     return out
 
 
 def assert_parity(got, ref, idx=None, cells=None, dt=None, cd=None, cfg=None):
-    e = cell_errors(got, ref, idx=idx)
+    e = fp64_score(got, ref, idx=idx)
     ns = got["n_sub"] if idx is None else got["n_sub"][idx]
     st = got["status"] if idx is None else got["status"][idx]
-    ok = (e <= RTOL) & (ns == ref["n_sub"]) & (st == ref["status"])
-    msg = (f"cells={e.size} frac_ok={ok.mean():.5f} max_err={e.max():.3e} p99={np.percentile(e, 99):.3e} "
+    ok = (e <= 1.0) & (ns == ref["n_sub"]) & (st == ref["status"])
+    msg = (f"cells={e.size} off_bar={(~ok).sum()} max_score={e.max():.3e} "
            f"nsub_mismatch={(ns != ref['n_sub']).sum()} status_mismatch={(st != ref['status']).sum()}")
     print(msg)
-    assert ok.mean() >= FRAC_OK, msg
-    assert e.max() <= HARD, msg
-    far = np.nonzero(e > SENSITIVE)[0]
-    assert far.size == 0 or cells is not None, msg
-    for j in far:
+    bad = np.nonzero(~ok)[0]
+    assert bad.size == 0 or cells is not None, msg
+    assert bad.size <= max(16, e.size // 200), msg      # the oracle replays each; keep the exception rare
+    for j in bad:
         i = j if idx is None else idx[j]
         cell = {k: cells[k][i] for k in inputs.FIELDS}
         dti = dt[i] if np.ndim(dt) else dt
-        sens = oracle_ulp_sensitivity(cell, dti, cd, cfg)
-        assert sens > 1e-9, f"cell {i}: error {e[j]:.2e} but oracle one-ulp sensitivity {sens:.2e}"
+        sens = oracle_rounding_sensitivity(cell, dti, cd, cfg)
+        print(f"cell {i}: score {e[j]:.2e}, n_sub {ns[j]} / {ref['n_sub'][j]}, oracle rounding sensitivity {sens:.2e}")
+        assert e[j] <= AMPLIFICATION * sens, f"cell {i}: score {e[j]:.2e} > {AMPLIFICATION:g} x sensitivity {sens:.2e}"
 
 
 def test_uniform_4096_cells_match_oracle():
@@ -67,12 +73,14 @@ def test_uniform_4096_cells_match_oracle():
     got = run_gpu(cells, 1e3 * YR, 1.0)
     assert_parity(got, ref, cells=cells, dt=1e3 * YR, cd=1.0)
     np.testing.assert_array_equal(got["y_Hp"], got["y_e"])
-    assert np.percentile(np.abs(got["y_Hm"] / ref["y_Hm"] - 1.0), 99.5) < 1e-9
+    assert np.abs(got["y_Hm"] / ref["y_Hm"] - 1.0).max() < 1e-9
     st = got["_stats"]
     assert st["cells"] == 4096 and st["substeps"] == int(got["n_sub"].sum())
     assert st["max_substeps"] == int(got["n_sub"].max())
-    assert abs(st["substeps"] / ref["n_sub"].sum() - 1.0) < 1e-3
-    assert abs(st["newton_iters"] / max(ref["n_itr"].sum(), 1) - 1.0) < 1e-2
+    assert st["substeps"] == int(ref["n_sub"].astype(np.int64).sum())
+    # the tight-coupling Newton iterations, cell by cell
+    assert np.array_equal(got["n_itr"], ref["n_itr"])
+    assert st["newton_iters"] == int(ref["n_itr"].astype(np.int64).sum())
 
 
 @pytest.mark.parametrize("n", [1, 31, 33, 4097])
@@ -177,3 +185,51 @@ def test_call_statistics_match_the_cells_and_the_oracle(precision):
         assert st["newton_iters"] == int(ref["n_itr"].astype(np.int64).sum())
     else:
         assert st["tight_cells"] > 0 and st["newton_iters"] > 0
+
+
+def _well_conditioned(cells, got, ref):
+    """Cells whose FP64 result meets the bar with the oracle's substep count."""
+    return np.nonzero((fp64_score(got, ref) <= 1.0) & (got["n_sub"] == ref["n_sub"]))[0]
+
+
+@pytest.mark.parametrize("no_reject", [False, True])
+def test_step_rejection_counts_and_the_literal_controller(no_reject):
+    """Reading of the small-change assumption of Eq. eq_deq (step rejection):
+    on the wide-range cells it fires in about 6 per cent of the cells.  The
+    statistics count the substeps it redid and their halvings exactly as the
+    oracle does (on the cells whose substep sequence is reproducible to the
+    FP64 bar); with SFCHEM_F_NO_REJECT (the controller exactly as Eq.
+    timestep_subcycle prints it) both counts are 0 and the cells meet the FP64
+    parity bar against the oracle in the same mode."""
+    import paper_2604_21438_gb300 as sf
+    cells = inputs.cells_extreme(4096, seed=2024)
+    dt, cd = 1e3 * YR, 1.0
+    kw = {"flags": sf.F_NO_REJECT} if no_reject else {}
+    cfg = oracle.default_config(flags=oracle.F_NO_REJECT if no_reject else 0)
+    ref = oracle.li_step(cells, dt, cd, cfg)
+    got = run_gpu(cells, dt, cd, **kw)
+    keep = _well_conditioned(cells, got, ref)
+    assert keep.size > 2000
+    sub = inputs.subset(cells, keep)
+    ref_k = {k: v[keep] for k, v in ref.items()}
+    got_k = run_gpu(sub, dt, cd, **kw)
+    assert_parity(got_k, ref_k, cells=sub, dt=dt, cd=cd, cfg=cfg)
+    st = got_k["_stats"]
+    assert st["rejected_substeps"] == int(ref_k["n_rej"].sum())
+    assert st["step_halvings"] == int(ref_k["n_halv"].sum())
+    if no_reject:
+        assert st["rejected_substeps"] == 0 and int(ref["n_rej"].sum()) == 0
+    else:
+        assert st["rejected_substeps"] > 50
+
+
+@pytest.mark.parametrize("flags", [0, 128])
+def test_grf_128cube_literal_controller_sampled(flags):
+    """The GRF grid with the controller as printed (no step rejection) against
+    the oracle in the same mode, 65,536 seeded cells plus every flagged one."""
+    cells = inputs.cells_grf(128, seed=1002)
+    cfg = oracle.default_config(flags=oracle.F_NO_REJECT if flags else 0)
+    got = run_gpu(cells, 1e3 * YR, 1.0, flags=flags)
+    idx = sample_with_flagged(got, len(cells["n_H"]), 65536, 23)
+    ref = oracle.li_step(inputs.subset(cells, idx), 1e3 * YR, 1.0, cfg)
+    assert_parity(got, ref, idx=idx, cells=cells, dt=1e3 * YR, cd=1.0, cfg=cfg)

@@ -1,30 +1,81 @@
-"""Mixed-precision path against the FP64 oracle (stated error bound), and
+"""Mixed-precision path against the FP64 oracle (stated error bounds), and
 determinism of the launch paths: the batched persistent kernel, the flat
 kernel, sharded launches on separate streams and replays of the captured
-graph all give bitwise identical cells (cells are independent)."""
+graph all give bitwise identical cells (cells are independent).
+
+Error metric (the thresholds of the mixed-precision workload description):
+per field, the relative error where the oracle's value exceeds 1e-8 and the
+absolute error where it does not, on T_g, T_d, E_IR, y_H2, y_e and y_H.
+The stated bounds (max, p99 and median of the relative error; max of the
+absolute one) are set per workload from measurements on 65,536 seeded cells
+plus every flagged cell, with a margin of about 2.  A cell may exceed the
+max bound only where the method itself cannot resolve it to that bound: the
+oracle's own result must move by more than the bound when f_chem (the
+substep factor of Eq. timestep_subcycle) changes by 1e-3 of itself.  Such
+cells sit at thermal instabilities, where a small change of the substep
+sequence moves the cell to another branch (measured: a GRF 128^3 cell at
+dt = 1e4 yr ends at 2.1e3 K or 1.4e4 K for f_chem = 0.03 or 0.0299)."""
 import numpy as np
 import pytest
 
 import inputs
 import oracle
-from _gpu_helpers import err_summary, run_gpu, sample_with_flagged
+from _gpu_helpers import mixed_errors, run_gpu, sample_with_flagged
 
 pytestmark = pytest.mark.gpu
 YR = inputs.YR
 FIELDS = ("T_g", "T_d", "E_IR", "y_H2", "y_e", "y_H")
-# Stated bound of the mixed path (relative error; abundances below 1e-6 in
-# units of 1e-6).  The median is set by the FP32 rates: a power T^p is taken
-# as exp(p ln T), and the rounding of ln T and of large exponents moves a
-# rate by 1e-7 to 1e-6, which y_H inherits in ionization balance (measured
-# medians: up to 3e-7, in the ionized core of the AMR workload).
-MIXED_MEDIAN, MIXED_P99, MIXED_MAX = 2e-6, 1e-3, 1e-2
+FCHEM_PROBE = 1e-3
+BOUND_GMC = dict(max=2e-5, p99=1e-6, median=1e-7, abs=1e-12)
+BOUND_AMR = dict(max=2e-4, p99=1e-5, median=1e-6, abs=1e-12)
+BOUND_RANDOM = dict(max=5e-3, p99=1e-4, median=1e-6, abs=1e-12)   # uniform and GRF draws
 
 
-def check_mixed(got, ref, idx=None):
-    s = err_summary(got, ref, small=1e-6, idx=idx)
-    print({k: (f"{v['max']:.2e}", f"{v['p99']:.2e}", f"{v['median']:.2e}") for k, v in s.items()})
-    for k, v in s.items():
-        assert v["median"] <= MIXED_MEDIAN and v["p99"] <= MIXED_P99 and v["max"] <= MIXED_MAX, (k, v)
+def fchem_sensitivity(cell, dt, cd, cfg=None):
+    """Largest relative change of the oracle's result (fields above 1e-8)
+    when f_chem changes by FCHEM_PROBE of itself, either way."""
+    one = {k: np.array([float(v)]) for k, v in cell.items()}
+    base_cfg = cfg or oracle.default_config()
+    r0 = oracle.li_step(one, dt, cd, base_cfg)
+    out = 0.0
+    for sgn in (1.0, -1.0):
+        c = oracle.default_config()
+        for name, _ in oracle.OracleConfig._fields_:
+            setattr(c, name, getattr(base_cfg, name))
+        c.f_chem = base_cfg.f_chem * (1.0 + sgn * FCHEM_PROBE)
+        r = oracle.li_step(one, dt, cd, c)
+        for k in FIELDS:
+            b = abs(r0[k][0])
+            if b > 1e-8:
+                out = max(out, abs(r[k][0] - r0[k][0]) / b)
+    return out
+
+
+def check_mixed(got, ref, idx=None, bound=BOUND_RANDOM, cells=None, dt=None, cd=None, cfg=None):
+    errs = mixed_errors(got, ref, idx=idx)
+    worst = np.zeros(len(ref["T_g"]))
+    report = {}
+    for k, (rel, ab) in errs.items():
+        r = rel[np.isfinite(rel)]
+        a = ab[np.isfinite(ab)]
+        report[k] = (float(r.max()) if r.size else 0.0, float(np.percentile(r, 99)) if r.size else 0.0,
+                     float(np.median(r)) if r.size else 0.0, float(a.max()) if a.size else 0.0)
+        worst = np.maximum(worst, np.nan_to_num(rel, nan=0.0))
+        assert report[k][1] <= bound["p99"] and report[k][2] <= bound["median"], (k, report[k], bound)
+        assert report[k][3] <= bound["abs"], (k, report[k], bound)
+    ns = got["n_sub"] if idx is None else got["n_sub"][idx]
+    print({k: tuple(f"{x:.2e}" for x in v) for k, v in report.items()},
+          f"n_sub mismatches: {int((ns != ref['n_sub']).sum())} of {ns.size}")
+    over = np.nonzero(worst > bound["max"])[0]
+    assert over.size <= max(4, worst.size // 500), (over.size, worst.max())
+    for j in over:
+        assert cells is not None, f"error {worst[j]:.2e} over the bound {bound['max']:.0e}"
+        i = j if idx is None else idx[j]
+        cell = {k: cells[k][i] for k in inputs.FIELDS}
+        dti = dt[i] if np.ndim(dt) else dt
+        sens = fchem_sensitivity(cell, dti, cd, cfg)
+        print(f"cell {i}: error {worst[j]:.2e}, oracle f_chem sensitivity {sens:.2e}")
+        assert sens > bound["max"], f"cell {i}: error {worst[j]:.2e} > {bound['max']:.0e}, sensitivity {sens:.2e}"
 
 
 @pytest.mark.parametrize("refine_ff", [False, True])
@@ -32,7 +83,7 @@ def test_mixed_uniform_4096(refine_ff):
     cells = inputs.cells_uniform(4096, seed=1001)
     ref = oracle.li_step(cells, 1e3 * YR, 1.0)
     got = run_gpu(cells, 1e3 * YR, 1.0, precision="mixed", flags=64 if refine_ff else 0)
-    check_mixed(got, ref)
+    check_mixed(got, ref, bound=BOUND_RANDOM, cells=cells, dt=1e3 * YR, cd=1.0)
     assert np.array_equal(got["status"] & 2, ref["status"] & 2)
 
 
@@ -40,9 +91,9 @@ def test_mixed_uniform_4096(refine_ff):
 def test_mixed_grf128_sampled(cd):
     cells = inputs.cells_grf(128, seed=1002)
     got = run_gpu(cells, 1e3 * YR, cd, precision="mixed")
-    idx = np.random.default_rng(8).choice(len(cells["n_H"]), 2048, replace=False)
+    idx = sample_with_flagged(got, len(cells["n_H"]), 65536, 8)
     ref = oracle.li_step(inputs.subset(cells, idx), 1e3 * YR, cd)
-    check_mixed(got, ref, idx=idx)
+    check_mixed(got, ref, idx=idx, bound=BOUND_RANDOM, cells=cells, dt=1e3 * YR, cd=cd)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -70,6 +121,49 @@ def test_batched_flat_and_sharded_are_bitwise_identical(precision):
     got = sf.to_host(d)
     for k in FIELDS + ("n_sub", "status"):
         assert np.array_equal(flat[k], got[k]), k
+    for sv in solvers:
+        sv.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_cost_balanced_partition_on_two_streams_is_bitwise(precision):
+    """The multi-device split of one workload (sfchem_partition on the
+    previous call's per-block substeps, sfchem_block_costs): the AMR block
+    list cut in two contiguous, cost-balanced ranges, each advanced by its own
+    context on its own stream, gives the single launch's cells bit for bit."""
+    import torch
+    import paper_2604_21438_gb300 as sf
+    cells, off, bdt, lvl = inputs.cells_amr(seed=1004)
+    n = len(cells["n_H"])
+    one = sf.Solver(precision)
+    d = sf.to_device(cells)
+    pristine = {k: d[k].clone() for k in sf.STATE_FIELDS}
+    one.step_batched(d, off, bdt, 100.0)
+    torch.cuda.synchronize()
+    ref = sf.to_host(d)
+    cost = one.block_costs(len(bdt)).astype(np.float64)
+    one.close()
+    # the costs are the blocks' substep sums
+    blk = np.searchsorted(off, np.arange(n), side="right") - 1
+    assert np.allclose(cost, np.bincount(blk, weights=ref["n_sub"], minlength=len(bdt)), rtol=1e-6)
+    cut = sf.partition(off, 2, cost)
+    load = [cost[cut[r]:cut[r + 1]].sum() for r in range(2)]
+    assert max(load) <= cost.sum() / 2 + cost.max()
+    for k in sf.STATE_FIELDS:
+        d[k].copy_(pristine[k])
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    solvers = [sf.Solver(precision), sf.Solver(precision)]
+    torch.cuda.synchronize()
+    for r in range(2):
+        b0, b1 = int(cut[r]), int(cut[r + 1])
+        c0, c1 = int(off[b0]), int(off[b1])
+        with torch.cuda.stream(streams[r]):
+            solvers[r].step_batched({k: v[c0:c1] for k, v in d.items()}, off[b0:b1 + 1] - off[b0], bdt[b0:b1],
+                                    100.0, stream=streams[r])
+    torch.cuda.synchronize()
+    got = sf.to_host(d)
+    for k in FIELDS + ("n_sub", "status", "n_itr"):
+        assert np.array_equal(ref[k], got[k]), k
     for sv in solvers:
         sv.close()
 
@@ -135,21 +229,20 @@ def test_gmc256_full_size_in_the_benchmark_launch(precision):
     idx = sample_with_flagged(got, len(cells["n_H"]), 65536, 17)
     ref = oracle.li_step(inputs.subset(cells, idx), 1e3 * YR, 100.0)
     if precision == "mixed":
-        check_mixed(got, ref, idx=idx)
+        check_mixed(got, ref, idx=idx, bound=BOUND_GMC, cells=cells, dt=1e3 * YR, cd=100.0)
     else:
-        from _gpu_helpers import cell_errors
-        e = cell_errors(got, ref, idx=idx)
-        assert (e <= 1e-9).mean() >= 0.995 and e.max() <= 1e-4, (e.max(), (e <= 1e-9).mean())
-        assert np.array_equal(got["n_sub"][idx], ref["n_sub"])
+        from test_gpu_fp64 import assert_parity
+        assert_parity(got, ref, idx=idx, cells=cells, dt=1e3 * YR, cd=100.0)
 
 
 def test_mixed_batched_amr_sampled():
     cells, off, bdt, lvl = inputs.cells_amr(seed=1004)
     got = run_gpu(cells, None, 100.0, precision="mixed", batched=(off, bdt))
-    idx = np.sort(np.random.default_rng(12).choice(len(cells["n_H"]), 2048, replace=False))
+    idx = sample_with_flagged(got, len(cells["n_H"]), 65536, 12)
     blk = np.searchsorted(off, idx, side="right") - 1
     ref = oracle.li_step(inputs.subset(cells, idx), bdt[blk], 100.0)
-    check_mixed(got, ref, idx=idx)
+    cell_dt = bdt[np.searchsorted(off, np.arange(len(cells["n_H"])), side="right") - 1]
+    check_mixed(got, ref, idx=idx, bound=BOUND_AMR, cells=cells, dt=cell_dt, cd=100.0)
 
 
 def test_mixed_masks_and_flags_general_kernel():
@@ -169,7 +262,7 @@ def test_mixed_masks_and_flags_general_kernel():
         ref = oracle.li_step(cells, 1e3 * YR, 100.0, cfg)
         got = run_gpu(cells, 1e3 * YR, 100.0, precision="mixed", **kw)
         print(kw)
-        check_mixed(got, ref)
+        check_mixed(got, ref, bound=BOUND_RANDOM, cells=cells, dt=1e3 * YR, cd=100.0, cfg=cfg)
 
 
 def test_all_on_and_general_kernels_agree():
@@ -182,5 +275,5 @@ def test_all_on_and_general_kernels_agree():
     a = run_gpu(cells, 1e3 * YR, 1.0, precision="mixed")
     b = run_gpu(cells, 1e3 * YR, 1.0, precision="mixed", reaction_mask=0xFFF & ~(1 << 9),
                 process_mask=sf.P_ALL & ~(1 << 1))
-    check_mixed(b, a)
+    check_mixed(b, a, bound=BOUND_RANDOM)
     assert (a["n_sub"] == b["n_sub"]).mean() >= 0.99
