@@ -31,3 +31,16 @@ def test_reference_arm_prints_one_contract_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_bench_states_the_tests_mixed_bounds():
+    """The bound bench.py reports against (largest relative error of the
+    mixed path per workload) is the one the parity tests enforce."""
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import bench
+    import test_gpu_mixed_batched as t
+    assert bench.STATED_MIXED_MAX == {"gmc256": t.BOUND_GMC["max"], "amr3000": t.BOUND_AMR["max"],
+                                      "be": t.BOUND_AMR["max"], "uniform4096": t.BOUND_RANDOM["max"],
+                                      "grf128": t.BOUND_RANDOM["max"]}
+    assert bench.FCHEM_PROBE == t.FCHEM_PROBE
