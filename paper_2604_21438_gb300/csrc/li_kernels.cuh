@@ -557,14 +557,32 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
     // again from the same state.
     // (the FP32 increments: a precise-pass correction is ~1e-7 of them)
     const W e0 = x[0] + dx[0], e1 = x[1] + dx[1], e2 = x[2] + dx[2];
-    const bool small = m_abs(e0) <= W(0.5) * fmax_w(S.uf[0], cw.y_floor) &&
-                       m_abs(e1) <= W(0.5) * fmax_w(S.uf[1], cw.y_floor) && e2 <= W(1) && e2 >= W(-0.5);
-    if (!small && c.nri < 30 && !(cfg.flags & F_NO_REJECT)) {
-      // rare: counted straight into the statistics (no per-lane registers)
-      if (c.nri == 0) atomicAdd(&stats->rejected, 1ull);
-      atomicAdd(&stats->halvings, 1ull);
-      c.nri++;
-      return false;
+    bool small = m_abs(e0) <= W(0.5) * fmax_w(S.uf[0], cw.y_floor) &&
+                 m_abs(e1) <= W(0.5) * fmax_w(S.uf[1], cw.y_floor) && e2 <= W(1) && e2 >= W(-0.5);
+    if constexpr (MIXED) {
+      // The conversions to FP64 below take finite values (to_f64).  e0-e2
+      // pass the tests above only when x and dx are finite in those rows;
+      // the T_d and E_IR rows are tested here, so a solution that is not
+      // finite (a NaN or an infinity from a singular or overflowing system)
+      // always reaches the rare branch below.
+      small = small && m_abs(x[3] + dx[3]) + m_abs(x[4] + dx[4]) < W(INFINITY);
+    }
+    if (!small) {
+      if constexpr (MIXED) {
+        // a solution that is not finite ends the cell as a bad substep, with
+        // its state as it was before the substep
+        W sa = W(0);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) sa += m_abs(x[i]) + m_abs(dx[i]);
+        if (!(sa < W(INFINITY))) { c.st |= ST_BADSTEP; return true; }
+      }
+      if (c.nri < 30 && !(cfg.flags & F_NO_REJECT)) {
+        // rare: counted straight into the statistics (no per-lane registers)
+        if (c.nri == 0) atomicAdd(&stats->rejected, 1ull);
+        atomicAdd(&stats->halvings, 1ull);
+        c.nri++;
+        return false;
+      }
     }
     c.nri = 0;
   }
@@ -614,8 +632,13 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
       W a3, a4;
       it = newton_dust_w<W>(a3, a4, S.uf[2] + d2, S.uf[3] + d3, S.uf[4] + d4, d3, d4, S.dTdg + (d3 - d2), dw,
                             c.k, cfg, cw.nr_tol);
-      c.u[3] = max_bits(u0[3] + to_f64(d3 + a3), TCMB);
-      c.u[4] = max_bits(u0[4] + to_f64(d4 + a4), EFLOOR);
+      // Newton corrections that are not finite end the cell as a bad
+      // substep, with the substep's (limited) LI update of T_d and E_IR in
+      // place of the iteration's (the conversions take finite values)
+      const bool fin = m_abs(a3) + m_abs(a4) < W(INFINITY);
+      c.u[3] = max_bits(u0[3] + to_f64(fin ? d3 + a3 : d3), TCMB);
+      c.u[4] = max_bits(u0[4] + to_f64(fin ? d4 + a4 : d4), EFLOOR);
+      if (!fin) { c.st |= ST_BADSTEP; return true; }
     } else {
       const double lam = damp_factor<double>(u0[3], u0[4], c.u[3] - u0[3], c.u[4] - u0[4]);
       if (lam < 1.0) {

@@ -91,20 +91,23 @@ extern "C" int sfbench_math_check(int fn, int n, const float *x, float *ours, fl
 }
 
 // The mixed path's integer conversions against the hardware ones: f2d_ours[i]
-// = f2d_int(xf[i]), f2d_ref[i] = (double)xf[i]; d2f_ours[i] = d2f_int(xd[i]),
-// d2f_ref[i] = __double2float_rn(xd[i]).  Host buffers of n elements each.
+// = f2d_int(xf[i]) (FIN: f2d_fin), f2d_ref[i] = (double)xf[i]; d2f_ours[i] =
+// d2f_int(xd[i]) (FIN: d2f_fin), d2f_ref[i] = __double2float_rn(xd[i]).  Host
+// buffers of n elements each.
+template <bool FIN>
 __global__ void conv_check(int n, const float *xf, double *f2d_ours, double *f2d_ref, const double *xd,
                            float *d2f_ours, float *d2f_ref) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  f2d_ours[i] = sfc::f2d_int(xf[i]);
+  f2d_ours[i] = FIN ? sfc::f2d_fin(xf[i]) : sfc::f2d_int(xf[i]);
   f2d_ref[i] = (double)xf[i];
-  d2f_ours[i] = sfc::d2f_int(xd[i]);
+  d2f_ours[i] = FIN ? sfc::d2f_fin(xd[i]) : sfc::d2f_int(xd[i]);
   d2f_ref[i] = __double2float_rn(xd[i]);
 }
 
-extern "C" int sfbench_conv_check(int n, const float *xf, double *f2d_ours, double *f2d_ref, const double *xd,
-                                  float *d2f_ours, float *d2f_ref) {
+namespace {
+int conv_check_run(bool fin, int n, const float *xf, double *f2d_ours, double *f2d_ref, const double *xd,
+                   float *d2f_ours, float *d2f_ref) {
   if (n <= 0 || !xf || !f2d_ours || !f2d_ref || !xd || !d2f_ours || !d2f_ref) return 1;
   const size_t N = (size_t)n;
   char *d = nullptr;
@@ -116,7 +119,10 @@ extern "C" int sfbench_conv_check(int n, const float *xf, double *f2d_ours, doub
   if (cudaMemcpy(dxf, xf, sizeof(float) * N, cudaMemcpyHostToDevice) != cudaSuccess) rc = 1;
   if (!rc && cudaMemcpy(dxd, xd, sizeof(double) * N, cudaMemcpyHostToDevice) != cudaSuccess) rc = 1;
   if (!rc) {
-    conv_check<<<(n + 255) / 256, 256>>>(n, dxf, dfo, dfr, dxd, ddo, ddr);
+    if (fin)
+      conv_check<true><<<(n + 255) / 256, 256>>>(n, dxf, dfo, dfr, dxd, ddo, ddr);
+    else
+      conv_check<false><<<(n + 255) / 256, 256>>>(n, dxf, dfo, dfr, dxd, ddo, ddr);
     if (cudaGetLastError() != cudaSuccess) rc = 1;
   }
   if (!rc && cudaMemcpy(f2d_ours, dfo, sizeof(double) * N, cudaMemcpyDeviceToHost) != cudaSuccess) rc = 1;
@@ -125,4 +131,15 @@ extern "C" int sfbench_conv_check(int n, const float *xf, double *f2d_ours, doub
   if (!rc && cudaMemcpy(d2f_ref, ddr, sizeof(float) * N, cudaMemcpyDeviceToHost) != cudaSuccess) rc = 1;
   cudaFree(d);
   return rc;
+}
+}  // namespace
+
+extern "C" int sfbench_conv_check(int n, const float *xf, double *f2d_ours, double *f2d_ref, const double *xd,
+                                  float *d2f_ours, float *d2f_ref) {
+  return conv_check_run(false, n, xf, f2d_ours, f2d_ref, xd, d2f_ours, d2f_ref);
+}
+
+extern "C" int sfbench_conv_check_fin(int n, const float *xf, double *f2d_ours, double *f2d_ref, const double *xd,
+                                      float *d2f_ours, float *d2f_ref) {
+  return conv_check_run(true, n, xf, f2d_ours, f2d_ref, xd, d2f_ours, d2f_ref);
 }

@@ -91,3 +91,41 @@ def test_integer_conversions_match_the_hardware():
     ta = do_[tie].astype(np.float64)
     assert np.all(np.abs(ta) > np.abs(xd[tie]))
     assert np.all(np.abs(ta - dr[tie].astype(np.float64)) <= np.spacing(np.abs(dr[tie])).astype(np.float64))
+
+
+def test_finite_conversions_match_the_hardware_on_finite_values():
+    """f2d_fin / d2f_fin (the substep loop's conversions, for finite values)
+    against CUDA's conversions on finite inputs: the same results as f2d_int
+    / d2f_int -- bitwise equal on normal numbers and zeros, subnormals to
+    signed zeros, d2f ties away from zero, values beyond the FP32 range to
+    signed infinities."""
+    from paper_2604_21438_gb300 import _build
+    _build.build()
+    L = ctypes.CDLL(_build.BENCH_LIB)
+    f32 = np.finfo(np.float32)
+    n = 1 << 20
+    xf = (10.0 ** RNG.uniform(-37.9, 38.5, n) * RNG.choice([-1.0, 1.0], n)).astype(np.float32)
+    xf[:6] = [0.0, -0.0, f32.tiny, -f32.max, 1e-40, -3e-39]
+    xd = 10.0 ** RNG.uniform(-37.9, 38.5, n) * RNG.choice([-1.0, 1.0], n)
+    t = (10.0 ** RNG.uniform(-30.0, 30.0, 1000)).astype(np.float32).astype(np.float64)
+    xd[8:1008] = t + 0.5 * np.spacing(t.astype(np.float32)).astype(np.float64)
+    xd[:6] = [0.0, -0.0, 3.5e38, -1e300, 1e-39, float(f32.max) * (1 + 2.0 ** -25)]
+    p = lambda a: ctypes.c_void_p(a.ctypes.data)
+    outs = []
+    for fn in (L.sfbench_conv_check, L.sfbench_conv_check_fin):
+        fo, fr, do_, dr = np.empty(n), np.empty(n), np.empty(n, np.float32), np.empty(n, np.float32)
+        assert fn(n, p(xf), p(fo), p(fr), p(xd), p(do_), p(dr)) == 0
+        outs.append((fo, fr, do_, dr))
+    (fo_i, fr, do_i, dr), (fo_f, _, do_f, _) = outs
+    # the finite versions agree with the complete ones bit for bit on finite inputs
+    assert np.array_equal(fo_f.view(np.uint64), fo_i.view(np.uint64))
+    assert np.array_equal(do_f.view(np.uint32), do_i.view(np.uint32))
+    # and with the hardware on normal numbers and zeros (f2d), outside the ties (d2f)
+    normal = (xf == 0) | (np.abs(xf) >= f32.tiny)
+    assert np.array_equal(fo_f[normal].view(np.uint64), fr[normal].view(np.uint64))
+    assert np.all(fo_f[~normal] == 0.0) and np.all(np.signbit(fo_f[~normal]) == np.signbit(xf[~normal]))
+    rest = np.ones(n, bool)
+    rest[8:1008] = False
+    rest &= ~(np.abs(xd) < f32.tiny) | (xd == 0)
+    assert np.array_equal(do_f[rest].view(np.uint32), dr[rest].view(np.uint32))
+    assert np.isinf(do_f[2]) and np.isinf(do_f[3]) and do_f[3] < 0 and do_f[4] == 0.0
