@@ -41,12 +41,12 @@ YR = inputs.YR
 # profiles/sfchem_li_mixed_gmc256.md, profiles/sfchem_li_fp64_gmc256.md.
 PROFILE_SOURCE = "ncu capture of the GMC-like 256^3 workload, first 512 blocks (profiles/)"
 WORK_PER_SUBSTEP = {
-    "mixed": {"fp32_flops": 1388.4, "fp64_flops": 30.2},
+    "mixed": {"fp32_flops": 1392.4, "fp64_flops": 30.2},
     "fp64": {"fp32_flops": 7.6, "fp64_flops": 2093.0},
 }
 # DRAM bytes per cell of one solver launch (same captures, 2,097,152 cells:
-# 291.4 MB mixed, 261.0 MB FP64).
-DRAM_BYTES_PER_CELL = {"mixed": 291.45e6 / 2097152, "fp64": 260.97e6 / 2097152}
+# 283.6 MB mixed, 261.0 MB FP64).
+DRAM_BYTES_PER_CELL = {"mixed": 283.60e6 / 2097152, "fp64": 260.97e6 / 2097152}
 # GB300 ALU peaks from unit counts and the SM clock: 152 SMs; FP32 128
 # lanes/SM (256 flops/clk); FP64 2 DFMA/clk/SM (4 flops/clk) -- the
 # "peak_sustained" of the FP64 pipe that ncu reports, 1.26 TFLOP/s at 2.07 GHz.
