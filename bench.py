@@ -47,9 +47,9 @@ WORK_PER_SUBSTEP = {
 # DRAM bytes per cell of one solver launch (same captures, 2,097,152 cells:
 # 283.6 MB mixed, 261.0 MB FP64).
 DRAM_BYTES_PER_CELL = {"mixed": 283.60e6 / 2097152, "fp64": 260.97e6 / 2097152}
-# DRAM bytes per cell of the photon kernel (ncu, first 1024 blocks of the
-# GMC-like grid: 48.0 B read, 10.9 B written; profiles/sfchem_photon_kernel_gmc256.md)
-PHOTON_DRAM_BYTES_PER_CELL = (201.35e6 + 45.66e6) / 4194304
+# DRAM bytes per cell of the photon kernel (ncu, one launch on the full
+# GMC-like grid: 48.0 B read, 14.7 B written; profiles/sfchem_photon_kernel_gmc256.md)
+PHOTON_DRAM_BYTES_PER_CELL = (805.33e6 + 246.62e6) / 16777216
 # GB300 ALU peaks from unit counts and the SM clock: 152 SMs; FP32 128
 # lanes/SM (256 flops/clk); FP64 2 DFMA/clk/SM (4 flops/clk) -- the
 # "peak_sustained" of the FP64 pipe that ncu reports, 1.26 TFLOP/s at 2.07 GHz.
@@ -378,8 +378,7 @@ def finish_line(args, rank, world, res, clk, n, cells, off, bdt, cd, desc, Z, ms
             "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": peaks["hbm_gbs"],
                          "frac": gbs / peaks["hbm_gbs"], "peak_source": src,
                          "bytes_per_cell": 64, "traffic": PHOTON_DRAM_BYTES_PER_CELL * n,
-                         "traffic_note": "ncu dram bytes per cell of a 4,194,304-cell launch x cells "
-                                         "(writes partly still in L2 there)"},
+                         "traffic_note": "ncu dram bytes per cell of one full-grid launch x cells"},
             "note": "photon consumption after the update (reading of Sec. 2.2.8), timed alone over 10 launches"}
     if "mixed_ff" in res:
         ms_f_max = allreduce_max(res["mixed_ff"]["ms"], world)
