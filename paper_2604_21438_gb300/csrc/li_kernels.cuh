@@ -207,7 +207,14 @@ __device__ __forceinline__ W damp_factor(W Td, W E, W dTd, W dE) {
 // start), dTg (T_d - T_g at the starting point) and dtw (the substep).  The
 // FP64 path forms them exactly from the FP64 state; the mixed path from its
 // W-precision view of the state and the LI increments.
-template <typename W>
+// POLISH: once the stopping test holds, one more full Newton step (not
+// counted) makes the FP64 result independent of the iteration at which the
+// test happened to pass (reading R11 of the oracle).  The mixed path stops at
+// the test: after a correction below 1e-5 of T_d, the iterate is within
+// ~1e-10 of the root, under its FP32 resolution, and the step costs 4.5 % of
+// the mixed kernel's time (measured T_d error on the GMC-like grid: p99
+// 1.06e-7 -> 1.32e-7, max 1.8e-7 -> 2.1e-7; the Newton counts are the same).
+template <typename W, bool POLISH>
 __device__ __forceinline__ int newton_dust_w(W &a3, W &a4, W T, W Tb, W Eb, W g3, W g4, W dTg, W dtw,
                                              const CellK<W> &c, const DevCfg &cfg, W tol) {
   typedef M<W> m;
@@ -256,7 +263,13 @@ __device__ __forceinline__ int newton_dust_w(W &a3, W &a4, W T, W Tb, W Eb, W g3
     // after the stopping test holds, one more full step (not counted) makes
     // the result independent of where the test happened to pass
     if (polish) { result = it - 1; break; }
-    if (lam == W(1) && m::abs(d0) <= tol * (Tb + a3) && m::abs(d1) <= tol * (Eb + a4)) polish = true;
+    if (lam == W(1) && m::abs(d0) <= tol * (Tb + a3) && m::abs(d1) <= tol * (Eb + a4)) {
+      if constexpr (!POLISH) {
+        result = it;
+        break;
+      }
+      polish = true;
+    }
   }
   return result;
 }
@@ -267,7 +280,7 @@ __device__ __forceinline__ int newton_dust(double u[5], const double u0[5], doub
                                            const DevCfg &cfg, double tol) {
   double a3, a4;
   const int it =
-      newton_dust_w<double>(a3, a4, u[2], u[3], u[4], u[3] - u0[3], u[4] - u0[4], u[3] - u[2], dt, c, cfg, tol);
+      newton_dust_w<double, true>(a3, a4, u[2], u[3], u[4], u[3] - u0[3], u[4] - u0[4], u[3] - u[2], dt, c, cfg, tol);
   u[3] = fmax(u[3] + a3, TCMB);
   u[4] = fmax(u[4] + a4, EFLOOR);
   return it;
@@ -630,7 +643,7 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
       const W d3 = lam * (S.uf[3] * x[3]), d4 = lam * (S.uf[4] * x[4]);
       const W d2 = S.uf[2] * x[2];
       W a3, a4;
-      it = newton_dust_w<W>(a3, a4, S.uf[2] + d2, S.uf[3] + d3, S.uf[4] + d4, d3, d4, S.dTdg + (d3 - d2), dw,
+      it = newton_dust_w<W, !MIXED>(a3, a4, S.uf[2] + d2, S.uf[3] + d3, S.uf[4] + d4, d3, d4, S.dTdg + (d3 - d2), dw,
                             c.k, cfg, cw.nr_tol);
       // Newton corrections that are not finite end the cell as a bad
       // substep, with the substep's (limited) LI update of T_d and E_IR in
