@@ -420,6 +420,11 @@ def finish_line(args, rank, world, res, clk, n, cells, off, bdt, cd, desc, Z, ms
     line["roofline"] = roofline(res, clk, n, "mixed", alg)
     if "fp64" in res:
         line["roofline_fp64"] = roofline(res, clk, n, "fp64", alg)
+    if "nr_fp64" in line and rank == 0 and not args.no_cpu:
+        try:
+            line["nr_fp64"]["roofline"] = roofline_nr(cells, off, bdt, cd, Z, n, line["nr_fp64"]["ms_per_step"], clk)
+        except Exception as exc:  # informational
+            line["nr_fp64"]["roofline_error"] = str(exc)
     if alg is not None:
         line["algorithmic_work"] = alg
     if rank == 0 and not args.no_cpu:
@@ -607,6 +612,26 @@ def algorithmic_work(cells, off, bdt, cd, Z=1.0, sample=256):
             "by_section_flops_per_substep": sec, "sample_cells": int(idx.size), "sample_substeps": r["substeps"],
             "how": "oracle LI step with an op-counting scalar type (oracle/opcount.cpp): forward-mode dual-number "
                    "Jacobian, equilibrated dense 5x5 elimination with two double-word refinements"}
+
+
+def roofline_nr(cells, off, bdt, cd, Z, n_cells, ms, clk, sample=256):
+    """Algorithmic roofline of the Newton-Raphson kernel (FP64): the oracle's
+    NR step counted with the op-counting scalar type on a seeded sample of
+    the workload (flops per cell), x cells / the kernel's CUDA-event time,
+    against the FP64 peak (unit counts x max SM clock)."""
+    import oracle
+    n = len(cells["n_H"])
+    idx = np.sort(np.random.default_rng(37).choice(n, min(sample, n), replace=False))
+    blk = np.searchsorted(off, idx, side="right") - 1
+    r = oracle.opcount(inputs.subset(cells, idx), bdt[blk], cd, oracle_config(Z), method="nr")
+    f_mhz = clk.get("sm_max_mhz") or 2070.0
+    peak64 = N_SM * FP64_FLOP_PER_SM_CLK * f_mhz * 1e6 / 1e12
+    w = r["per_cell"]["flops"]
+    ach = w * n_cells / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "unit": "TFLOP/s", "kernel": "sfchem_nr_fp64", "pipe": "fp64", "achieved": ach,
+            "peak": peak64, "frac": ach / peak64, "W_flops_per_cell": w,
+            "W_transcendentals_per_cell": r["per_cell"]["transcendentals"], "sample_cells": int(idx.size),
+            "work": "algorithmic: oracle NR step op count per cell x cells of the launch"}
 
 
 # ------------------------------------------------------------ reference arm

@@ -104,39 +104,42 @@ def build_opcount(force: bool = False) -> str:
     return _OPC_LIB
 
 
-def opcount(cells: dict, dt, cd_factor: float = 1.0, cfg: OracleConfig | None = None) -> dict:
-    """Floating-point operations of the oracle's LI step on these cells,
-    counted by type and section (single thread).  Returns {"substeps": N,
-    "counts": {section: {op: count}}, "per_substep": {...}} where flops count
-    add/sub, mul and div as 1 and fma as 2, and sqrt / exp / log / pow are
-    reported apart."""
+def opcount(cells: dict, dt, cd_factor: float = 1.0, cfg: OracleConfig | None = None, method: str = "li") -> dict:
+    """Floating-point operations of the oracle's LI step (method "li") or
+    Newton-Raphson step ("nr") on these cells, counted by type and section
+    (single thread).  Returns {"substeps": N, "cells": valid cells,
+    "counts": {section: {op: count}}, "per_substep": {...}, "per_cell": {...}}
+    where flops count add/sub, mul and div as 1 and fma as 2, and sqrt /
+    exp / log / pow are reported apart."""
     global _opc
     if _opc is None:
         build_opcount()
         L = ctypes.CDLL(_OPC_LIB)
         L.oracle_opcount_li.restype = ctypes.c_int64
+        L.oracle_opcount_nr.restype = ctypes.c_int64
         _opc = L
+    fn = {"li": _opc.oracle_opcount_li, "nr": _opc.oracle_opcount_nr}[method]
     cfg = cfg or default_config()
     n = len(cells["n_H"])
     a = {k: np.ascontiguousarray(cells[k], dtype=np.float64) for k in FIELDS_IN + FIELDS_STATE}
     dtv = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
     counts = np.zeros((len(OPCOUNT_SECTIONS), len(OPCOUNT_OPS)), np.uint64)
-    nsub = _opc.oracle_opcount_li(
+    nsub = fn(
         ctypes.c_int64(n), _p(a["n_H"]), _p(a["T_g"]), _p(a["T_d"]), _p(a["E_IR"]), _p(a["y_H2"]), _p(a["y_e"]),
         _p(a["G0"]), _p(a["n_EUV"]), _p(a["N_H2"]), _p(dtv), ctypes.c_double(cd_factor), ctypes.byref(cfg),
         _p(counts))
     if nsub < 0:
-        raise ValueError("oracle_opcount_li rejected its arguments")
-    out = {"substeps": int(nsub), "counts": {}, "per_substep": {}}
+        raise ValueError(f"oracle_opcount_{method} rejected its arguments")
+    out = {"substeps": int(nsub), "cells": int(n), "counts": {}, "per_substep": {}, "per_cell": {}}
     tot = np.zeros(len(OPCOUNT_OPS))
     for i, sec in enumerate(OPCOUNT_SECTIONS):
         out["counts"][sec] = {op: int(counts[i, j]) for j, op in enumerate(OPCOUNT_OPS)}
         tot += counts[i]
-    per = tot / max(nsub, 1)
-    d = dict(zip(OPCOUNT_OPS, per))
-    out["per_substep"] = {op: float(v) for op, v in d.items()}
-    out["per_substep"]["flops"] = float(d["add"] + d["mul"] + d["div"] + 2 * d["fma"])
-    out["per_substep"]["transcendentals"] = float(d["sqrt"] + d["exp"] + d["log"] + d["pow"])
+    for key, den in (("per_substep", max(nsub, 1)), ("per_cell", max(n, 1))):
+        d = dict(zip(OPCOUNT_OPS, tot / den))
+        out[key] = {op: float(v) for op, v in d.items()}
+        out[key]["flops"] = float(d["add"] + d["mul"] + d["div"] + 2 * d["fma"])
+        out[key]["transcendentals"] = float(d["sqrt"] + d["exp"] + d["log"] + d["pow"])
     return out
 
 

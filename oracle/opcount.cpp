@@ -111,4 +111,27 @@ int64_t oracle_opcount_li(int64_t n, const double *n_H, const double *T_g, const
   return nsub;
 }
 
+// Counted Newton-Raphson backward-Euler step (the paper's reference solver,
+// nr_cell) of n cells, one after another (single thread); counts as above,
+// by the section of the oracle function that runs each operation; returns
+// the total number of accepted steps, or -1 on a bad argument.
+int64_t oracle_opcount_nr(int64_t n, const double *n_H, const double *T_g, const double *T_d, const double *E_IR,
+                          const double *y_H2, const double *y_e, const double *G0, const double *n_EUV,
+                          const double *N_H2, const double *dt, double cd_factor, const oracle_config *cfg,
+                          uint64_t *counts) {
+  if (n < 0 || !counts || !(cd_factor > 0.0)) return -1;
+  oracle_config c = checked(cfg);
+  std::memset(ocount::g_count, 0, sizeof(ocount::g_count));
+  int64_t nsub = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!valid_input(n_H[i], T_g[i], T_d[i], E_IR[i], y_H2[i], y_e[i], G0[i], n_EUV[i], N_H2[i], dt[i])) continue;
+    CellIn ci = make_cell(n_H[i], G0[i], n_EUV[i], N_H2[i], cd_factor, c);
+    real u[5] = {y_H2[i], y_e[i], T_g[i], T_d[i], E_IR[i]};
+    LIOut o = nr_cell(u, ci, dt[i], c);
+    nsub += o.nsub;
+  }
+  std::memcpy(counts, ocount::g_count, sizeof(ocount::g_count));
+  return nsub;
+}
+
 }  // extern "C"
