@@ -6,8 +6,15 @@
 
 namespace sfc {
 
-// One kernel for every launch shape (64 or 128 threads per CTA).
-__global__ void __launch_bounds__(128) sfchem_nr_fp64(KArgs a) { li_persistent_body<double, false, true>(a); }
+// One kernel for every launch shape (64 or 128 threads per CTA), at full
+// occupancy (32 registers, 64 warps per SM).  The nested Newton loops are a
+// long body whose lanes take different iteration counts, so warps wait for
+// instruction fetch far more than for the FP64 pipe: more warps hide it
+// despite the spills (GMC-like 256^3, first 512 blocks: 186 ms with 166
+// registers and 12 warps per SM, 164 / 138 / 114 ms with 96 / 64 / 32
+// registers).  The FP64 LI kernel, bound by its FP64 pipe, gains nothing
+// from the same change (it slows down).
+__global__ void __launch_bounds__(128, 16) sfchem_nr_fp64(KArgs a) { li_persistent_body<double, false, true>(a); }
 
 cudaError_t launch_nr_fp64(const KArgs &a, int grid, int tpb, cudaStream_t s) {
   if (tpb != 64 && tpb != 128) return cudaErrorInvalidValue;
