@@ -260,8 +260,9 @@ __device__ __forceinline__ int newton_dust_w(W &a3, W &a4, W T, W Tb, W Eb, W g3
     const W lam = polish ? W(1) : damp_factor<W>(Td, E, d0, d1);
     a3 = fmax_w(Tb + (a3 + lam * d0), W(TCMB)) - Tb;
     a4 = fmax_w(Eb + (a4 + lam * d1), W(EFLOOR)) - Eb;
-    // after the stopping test holds, one more full step (not counted) makes
-    // the result independent of where the test happened to pass
+    // with POLISH, after the stopping test holds, one more full step (not
+    // counted) makes the result independent of where the test happened to
+    // pass; without it the iteration ends at the test
     if (polish) { result = it - 1; break; }
     if (lam == W(1) && m::abs(d0) <= tol * (Tb + a3) && m::abs(d1) <= tol * (Eb + a4)) {
       if constexpr (!POLISH) {
