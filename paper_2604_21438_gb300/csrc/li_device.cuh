@@ -74,13 +74,29 @@ struct DevCfg {
 };
 
 // ------------------------------------------------------- precision wrappers
+// FP64 reciprocal estimate of the PTX ISA (rcp.approx.ftz.f64); the FP64
+// reciprocal below refines it by Newton-Raphson.
+__device__ __forceinline__ double ptx_rcp64(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return y;
+}
 template <typename W> struct M;
 template <> struct M<double> {
   static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
   static __device__ __forceinline__ double log(double x) { return ::log(x); }
   static __device__ __forceinline__ double log1p(double x) { return ::log1p(x); }
   static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
-  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  // 1/x for finite non-zero x: two Newton-Raphson steps r' = r + r (1 - x r)
+  // on the hardware estimate (each squares the relative error), within 1 ulp
+  // of the IEEE quotient (tests/test_gpu_math.py), in fewer FP64 pipe slots
+  // than the IEEE division: the FP64 kernels are bound by that pipe and take
+  // ~30 reciprocals per substep.  0 and infinities are not handled.
+  static __device__ __forceinline__ double rcp(double x) {
+    double r = ptx_rcp64(x);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return fma(r, fma(-x, r, 1.0), r);
+  }
   static __device__ __forceinline__ double abs(double x) { return ::fabs(x); }
 };
 // FP32 (mixed path): the hardware approximations of the PTX ISA (ex2, lg2,
@@ -199,10 +215,10 @@ template <> __device__ __forceinline__ float to_w<float>(double d) { return d2f_
 __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return f2d_fin(x); }
 
-// a / b: IEEE division in FP64; in FP32 a times the corrected reciprocal
-// (within 2 ulp, and a fraction of the instructions of an IEEE division),
-// for b > 0 finite
-__device__ __forceinline__ double div_w(double a, double b) { return a / b; }
+// a / b as a times the refined reciprocal in both precisions (within 2 ulp
+// of the IEEE quotient, and a fraction of the instructions of an IEEE
+// division), for b > 0 finite
+__device__ __forceinline__ double div_w(double a, double b) { return a * M<double>::rcp(b); }
 __device__ __forceinline__ float div_w(float a, float b) { return a * M<float>::rcp(b); }
 
 __device__ __forceinline__ double fmax_w(double a, double b) { return ::fmax(a, b); }

@@ -60,6 +60,7 @@ extern "C" int sfbench_fma_fp32(int iters, double *flops_per_s, float *ms) {
 
 // fn: 0 exp, 1 log, 2 rcp, 3 sqrt.  ours[i] = the solver's M<float> function
 // of x[i], ref[i] = CUDA's expf / logf / 1.0f / x / sqrtf.  Host buffers.
+// sfbench_rcp64_check: ours[i] = M<double>::rcp(x[i]), ref[i] = 1.0 / x[i].
 __global__ void math_check(int fn, int n, const float *x, float *ours, float *ref) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -142,4 +143,27 @@ extern "C" int sfbench_conv_check(int n, const float *xf, double *f2d_ours, doub
 extern "C" int sfbench_conv_check_fin(int n, const float *xf, double *f2d_ours, double *f2d_ref, const double *xd,
                                       float *d2f_ours, float *d2f_ref) {
   return conv_check_run(true, n, xf, f2d_ours, f2d_ref, xd, d2f_ours, d2f_ref);
+}
+
+__global__ void rcp64_check(int n, const double *x, double *ours, double *ref) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  ours[i] = sfc::M<double>::rcp(x[i]);
+  ref[i] = 1.0 / x[i];
+}
+
+extern "C" int sfbench_rcp64_check(int n, const double *x, double *ours, double *ref) {
+  if (n <= 0 || !x || !ours || !ref) return 1;
+  double *d = nullptr;
+  if (cudaMalloc(&d, sizeof(double) * 3 * (size_t)n) != cudaSuccess) return 1;
+  int rc = 0;
+  if (cudaMemcpy(d, x, sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess) rc = 1;
+  if (!rc) {
+    rcp64_check<<<(n + 255) / 256, 256>>>(n, d, d + n, d + 2 * (size_t)n);
+    if (cudaGetLastError() != cudaSuccess) rc = 1;
+  }
+  if (!rc && cudaMemcpy(ours, d + n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess) rc = 1;
+  if (!rc && cudaMemcpy(ref, d + 2 * (size_t)n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess) rc = 1;
+  cudaFree(d);
+  return rc;
 }

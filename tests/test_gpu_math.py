@@ -129,3 +129,20 @@ def test_finite_conversions_match_the_hardware_on_finite_values():
     rest &= ~(np.abs(xd) < f32.tiny) | (xd == 0)
     assert np.array_equal(do_f[rest].view(np.uint32), dr[rest].view(np.uint32))
     assert np.isinf(do_f[2]) and np.isinf(do_f[3]) and do_f[3] < 0 and do_f[4] == 0.0
+
+
+def test_fp64_reciprocal_within_one_ulp():
+    """M<double>::rcp (two Newton-Raphson steps on rcp.approx.ftz.f64, the
+    FP64 kernels' reciprocal and division) against the IEEE quotient 1/x,
+    over the normal range the solver uses."""
+    from paper_2604_21438_gb300 import _build
+    _build.build()
+    L = ctypes.CDLL(_build.BENCH_LIB)
+    n = 1 << 20
+    x = 10.0 ** RNG.uniform(-300.0, 300.0, n) * RNG.choice([-1.0, 1.0], n)
+    x[:6] = [1.0, -1.0, 3.0, 2.725, 1e-14, 1e300]
+    ours, ref = np.empty(n), np.empty(n)
+    p = lambda a: ctypes.c_void_p(a.ctypes.data)
+    assert L.sfbench_rcp64_check(n, p(np.ascontiguousarray(x)), p(ours), p(ref)) == 0
+    ulp = np.abs(ours - ref) / np.spacing(np.abs(ref))
+    assert ulp.max() <= 1.0
