@@ -42,11 +42,11 @@ YR = inputs.YR
 PROFILE_SOURCE = "ncu capture of the GMC-like 256^3 workload, first 512 blocks (profiles/)"
 WORK_PER_SUBSTEP = {
     "mixed": {"fp32_flops": 1303.4, "fp64_flops": 30.2},
-    "fp64": {"fp32_flops": 7.6, "fp64_flops": 2093.0},
+    "fp64": {"fp32_flops": 1.6, "fp64_flops": 2017.7},
 }
 # DRAM bytes per cell of one solver launch (same captures, 2,097,152 cells:
-# 284.2 MB mixed, 261.0 MB FP64).
-DRAM_BYTES_PER_CELL = {"mixed": 284.18e6 / 2097152, "fp64": 260.97e6 / 2097152}
+# 284.2 MB mixed, 263.8 MB FP64).
+DRAM_BYTES_PER_CELL = {"mixed": 284.18e6 / 2097152, "fp64": 263.81e6 / 2097152}
 # DRAM bytes per cell of the photon kernel (ncu, one launch on the full
 # GMC-like grid: 48.0 B read, 14.7 B written; profiles/sfchem_photon_kernel_gmc256.md)
 PHOTON_DRAM_BYTES_PER_CELL = (805.33e6 + 246.62e6) / 16777216
