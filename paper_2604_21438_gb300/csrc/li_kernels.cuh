@@ -231,7 +231,6 @@ __device__ __forceinline__ int newton_dust_w(W &a3, W &a4, W T, W Tb, W Eb, W g3
   for (int it = 1; it <= cfg.nr_itr_limit + 1; ++it) {
     if (it > cfg.nr_itr_limit && !polish) break;
     const W Td = Tb + a3, E = Eb + a4;
-    const W rTd = m::rcp(Td), rE = m::rcp(E);
     W be_d, ba_d, be_i, ba_i;
     const W kd = kappa_w<W>(Td, be_d, ba_d);
     const W TIR = m::sqrt(m::sqrt(W(1e-4 / ARAD) * E));
@@ -243,20 +242,24 @@ __device__ __forceinline__ int newton_dust_w(W &a3, W &a4, W T, W Tb, W Eb, W g3
     const W beta_IR = (pm & P_IRABS) ? ba_i : W(0);
     const W D = irabs + c.EUV - emit - G * gam * (dTg + a3);
     const W I = rho * fd * (emit - irabs);
-    // relative unknowns (dT_d/T_d, dE/E); rows scaled by C_d T_d and E
-    W r0 = (-(g3 + a3) + dtw * D * c.rCd) * rTd;
-    W r1 = (-(g4 + a4) + dtw * I) * rE;
+    // Newton system in the corrections (dT_d, dE_IR) themselves, the dust
+    // row divided by C_d: J00 and J11 are the diagonals of the relative
+    // system, K01 = J01 T_d / E_IR and K10 = J10 E_IR / T_d its off-diagonals
+    // with the scalings cancelled, so that no reciprocal of T_d or E_IR is
+    // needed (the same determinant; Cramer's rule is scale-invariant)
+    W R0 = -(g3 + a3) + dtw * D * c.rCd;
+    W R1 = -(g4 + a4) + dtw * I;
     W J00 = W(1) + dtw * (G * gam + acTd3 * beta_d) * c.rCd;
-    W J01 = -dtw * W(CRED) * beta_IR * E * c.rCd * rTd;
-    W J10 = -dtw * rho * fd * acTd3 * beta_d * Td * rE;
+    W K01 = -dtw * W(CRED) * beta_IR * c.rCd;
+    W K10 = -dtw * rho * fd * acTd3 * beta_d;
     W J11 = W(1) + dtw * rho * W(CRED) * fd * beta_IR;
-    if (frTd) { J00 = W(1); J01 = W(0); r0 = W(0); }
-    if (frE) { J10 = W(0); J11 = W(1); r1 = W(0); }
-    const W det = J00 * J11 - J01 * J10;
+    if (frTd) { J00 = W(1); K01 = W(0); R0 = W(0); }
+    if (frE) { K10 = W(0); J11 = W(1); R1 = W(0); }
+    const W det = J00 * J11 - K01 * K10;
     if (!(m::abs(det) > W(0))) { result = -it; break; }
     const W rdet = m::rcp(det);
-    const W d0 = (r0 * J11 - J01 * r1) * rdet * Td;
-    const W d1 = (J00 * r1 - J10 * r0) * rdet * E;
+    const W d0 = (R0 * J11 - K01 * R1) * rdet;
+    const W d1 = (J00 * R1 - K10 * R0) * rdet;
     const W lam = polish ? W(1) : damp_factor<W>(Td, E, d0, d1);
     a3 = fmax_w(Tb + (a3 + lam * d0), W(TCMB)) - Tb;
     a4 = fmax_w(Eb + (a4 + lam * d1), W(EFLOOR)) - Eb;
