@@ -366,7 +366,7 @@ def finish_line(args, rank, world, res, clk, n, cells, off, bdt, cd, desc, Z, ms
             "value": total_cells / (e2e_max * 1e-3), "unit": "cell-updates/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max,
             "path": "sfchem_step_host: pinned host state, copies overlapped with the solver slice by slice"},
-        "gpu_launches": 2 * args.steps,   # per step: schedule kernel + persistent solver kernel
+        "gpu_launches": 3 * args.steps,   # per step: schedule kernel, persistent solver kernel, y_H- kernel
         "clocks": clk,
     }
     if "photon" in res:

@@ -19,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsfchem.so")
 BENCH_LIB = os.path.join(HERE, "libsfbench.so")
 UNITS = ("li_fp64.cu", "li_mixed.cu", "li_mixed_ff.cu", "li_mixed_masked.cu", "nr_fp64.cu", "sfchem_abi.cu",
-         "noalloc.cu", "photon.cu")
+         "noalloc.cu", "photon.cu", "derived.cu")
 BENCH_UNITS = ("microbench.cu",)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]

@@ -13,7 +13,8 @@ __global__ void __launch_bounds__(128) sfchem_li_fp64(KArgs a) { li_persistent_b
 cudaError_t launch_li_fp64(const KArgs &a, int grid, int tpb, cudaStream_t s) {
   if (tpb != 64 && tpb != 128) return cudaErrorInvalidValue;
   sfchem_li_fp64<<<grid, tpb, 0, s>>>(a);
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? launch_hminus(a, false, s) : e;
 }
 
 cudaError_t occupancy_li_fp64(int tpb, int *ctas_per_sm) {

@@ -5,8 +5,9 @@
 // chunks of cells from a global counter (one atomic per chunk).  Inside a
 // warp every lane owns one cell and advances it one LI substep per loop
 // trip; a lane whose cell has reached dt_hydro stores it and is refilled from
-// the warp's chunk before the next trip (warp-vote refill), so lanes with
-// long substep sequences do not hold idle lanes hostage.  There are no waits
+// the warp's chunk (warp-vote refill; the mixed kernel waits until a few
+// lanes are idle and serves them together), so lanes with long substep
+// sequences do not hold idle lanes hostage.  There are no waits
 // on other threads anywhere, so the kernel always terminates: every cell
 // loop is bounded by n_sub_max, every Newton loop by nr_itr_limit.
 #pragma once
@@ -676,10 +677,15 @@ __device__ __forceinline__ bool li_substep(CellRun<W> &c, const DevCfg &cfg, con
 }
 
 // H- abundance from the equilibrium of reactions H2 and H3 (unmasked rates)
+// at the gas temperature: y_H- = k_H2 y_e / k_H3.  Formed for every finished
+// cell by a separate elementwise kernel after the solver (derived.cu): in the
+// solver it ran once per finished cell with a few lanes of the warp active,
+// code outside the substep loop that also evicted the loop from the
+// instruction cache (4 % of the mixed kernel's time, 7 % of the FP64 one's).
 template <typename W>
-__device__ __forceinline__ double y_hminus(double Td, double ye) {
+__device__ __forceinline__ double y_hminus(double Tg, double ye) {
   typedef M<W> m;
-  const W T = to_w<W>(Td);
+  const W T = to_w<W>(Tg);
   const W lnT = m::log(T);
   const W k2 = m::exp(W(-41.11005943727161) + W(0.928) * lnT - T * W(1.0 / 16200.0));
   const W N = m::exp(W(0.098493) * lnT) + W(0.32852) * m::exp(W(0.5561) * lnT) +
@@ -753,8 +759,47 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
                      s_bad = 0, s_badstep = 0;
   unsigned int s_max = 0;
 
+  // A lane whose cell is finished stores it and takes a new one in the
+  // warp's refill phase; that code runs with only the idle lanes active and
+  // lies outside the substep loop, so each pass costs about as much as a
+  // substep of the whole warp and evicts the loop from the instruction cache.
+  // The mixed kernel therefore lets finished lanes wait (pend) until
+  // REFILL_MIN lanes are idle and serves them in one pass.  Measured on the
+  // GMC-like grid (the same results bit for bit): with y_H- still formed in
+  // the store, waiting for 3 / 4 / 6 / 8 / 12 idle lanes took 5.5 / 7.0 /
+  // 7.6 / 6.6 / 1.2 % off the kernel's time; with y_H- formed after the
+  // solver (derived.cu), 3 / 4 / 5 / 6 / 8 lanes gave 73.7 / 73.1 / 72.9 /
+  // 73.1 / 74.1 ms.  The FP64 kernels spend ~40x longer per substep, so a
+  // pass is cheap for them and waiting is not: they refill at once.  All
+  // lanes idle always makes a pass, so every finished cell is stored before
+  // the warp leaves the loop.
+  constexpr int REFILL_MIN = (MIXED && !NR) ? 4 : 1;
+  bool pend = false;
   while (true) {
     unsigned need = __ballot_sync(FULL, !have);
+    if (__popc(need) < REFILL_MIN && need != FULL) need = 0u;
+    if (need != 0u && pend) {
+      if constexpr (MIXED && !NR) {
+        // the bound y_H2 <= (1 - y_e)/2 not yet applied to the last update
+        if (__double_as_longlong(fma(-2.0, c.u[0], 1.0) - c.u[1]) < 0) c.u[0] = (1.0 - c.u[1]) * 0.5;
+      }
+      a.y2[idx] = c.u[0]; a.ye[idx] = c.u[1]; a.Tg[idx] = c.u[2]; a.Td[idx] = c.u[3]; a.E[idx] = c.u[4];
+      if (a.yH) a.yH[idx] = 1.0 - 2.0 * c.u[0] - c.u[1];
+      if (a.yHp) a.yHp[idx] = c.u[1];
+      if (a.yHm) a.yHm[idx] = 0.0;   // marks a valid cell: y_H- is formed after the solver
+      if (a.status) a.status[idx] = c.st;
+      if (a.nsub) a.nsub[idx] = c.nsub;
+      if (a.niter) a.niter[idx] = c.nitr;
+      s_sub += (unsigned long long)c.nsub;
+      s_newton += (unsigned long long)c.nitr;
+      s_max = max(s_max, (unsigned int)c.nsub);
+      if (c.st & ST_TIGHT) s_tight++;
+      if (c.st & ST_CAP) s_cap++;
+      if (c.st & ST_NOCONV) s_noconv++;
+      if (c.st & ST_BADSTEP) s_badstep++;
+      if (a.block_cost && blk >= 0) atomicAdd(a.block_cost + blk, (float)c.nsub);
+      pend = false;
+    }
     while (need != 0u && !exhausted) {
       if (cpos >= cend) {
         unsigned long long ci = 0;
@@ -803,7 +848,7 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
             a.y2[idx] = c.u[0]; a.ye[idx] = c.u[1]; a.Tg[idx] = c.u[2]; a.Td[idx] = c.u[3]; a.E[idx] = c.u[4];
             if (a.yH) a.yH[idx] = 1.0 - 2.0 * c.u[0] - c.u[1];
             if (a.yHp) a.yHp[idx] = c.u[1];
-            if (a.yHm) a.yHm[idx] = y_hminus<W>(c.u[2], c.u[1]);
+            if (a.yHm) a.yHm[idx] = 0.0;   // formed after the solver (derived.cu)
             if (a.status) a.status[idx] = 0;
             if (a.nsub) a.nsub[idx] = 0;
             if (a.niter) a.niter[idx] = 0;
@@ -819,26 +864,8 @@ __device__ __forceinline__ void li_persistent_body(const KArgs &a) {
       if constexpr (NR) done = nr_attempt(c, cfg, cw);
       else done = li_substep<W, MIXED, RF>(c, cfg, cw, a.stats);
       if (done) {
-        if constexpr (MIXED && !NR) {
-          // the bound y_H2 <= (1 - y_e)/2 not yet applied to the last update
-          if (__double_as_longlong(fma(-2.0, c.u[0], 1.0) - c.u[1]) < 0) c.u[0] = (1.0 - c.u[1]) * 0.5;
-        }
-        a.y2[idx] = c.u[0]; a.ye[idx] = c.u[1]; a.Tg[idx] = c.u[2]; a.Td[idx] = c.u[3]; a.E[idx] = c.u[4];
-        if (a.yH) a.yH[idx] = 1.0 - 2.0 * c.u[0] - c.u[1];
-        if (a.yHp) a.yHp[idx] = c.u[1];
-        if (a.yHm) a.yHm[idx] = y_hminus<W>(c.u[2], c.u[1]);
-        if (a.status) a.status[idx] = c.st;
-        if (a.nsub) a.nsub[idx] = c.nsub;
-        if (a.niter) a.niter[idx] = c.nitr;
-        s_sub += (unsigned long long)c.nsub;
-        s_newton += (unsigned long long)c.nitr;
-        s_max = max(s_max, (unsigned int)c.nsub);
-        if (c.st & ST_TIGHT) s_tight++;
-        if (c.st & ST_CAP) s_cap++;
-        if (c.st & ST_NOCONV) s_noconv++;
-        if (c.st & ST_BADSTEP) s_badstep++;
-        if (a.block_cost && blk >= 0) atomicAdd(a.block_cost + blk, (float)c.nsub);
         have = false;
+        pend = true;
       }
     }
   }

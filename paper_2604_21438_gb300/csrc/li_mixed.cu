@@ -32,10 +32,16 @@ static bool all_on(const DevCfg &c) {
 
 cudaError_t launch_li_mixed(const KArgs &a, int grid, int tpb, cudaStream_t s) {
   if (tpb != 64 && tpb != 128) return cudaErrorInvalidValue;
-  if (!all_on(a.cfg)) return launch_li_mixed_masked(a, grid, tpb, s);
-  if (a.cfg.flags & F_REFINE_FF) return launch_li_mixed_ff(a, grid, tpb, s);
-  sfchem_li_mixed<<<grid, tpb, 0, s>>>(a);
-  return cudaGetLastError();
+  cudaError_t e;
+  if (!all_on(a.cfg)) {
+    e = launch_li_mixed_masked(a, grid, tpb, s);
+  } else if (a.cfg.flags & F_REFINE_FF) {
+    e = launch_li_mixed_ff(a, grid, tpb, s);
+  } else {
+    sfchem_li_mixed<<<grid, tpb, 0, s>>>(a);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? launch_hminus(a, true, s) : e;
 }
 
 // the smallest residency of the three instances, so that one launch shape fits all

@@ -96,9 +96,10 @@ def test_integer_conversions_match_the_hardware():
 def test_finite_conversions_match_the_hardware_on_finite_values():
     """f2d_fin / d2f_fin (the substep loop's conversions, for finite values)
     against CUDA's conversions on finite inputs: the same results as f2d_int
-    / d2f_int -- bitwise equal on normal numbers and zeros, subnormals to
-    signed zeros, d2f ties away from zero, values beyond the FP32 range to
-    signed infinities."""
+    / d2f_int -- bitwise equal on normal numbers and zeros, d2f ties away from
+    zero, values beyond the FP32 range to signed infinities -- except that
+    f2d_fin takes an FP32 subnormal m 2^-149 to the FP64 subnormal m 2^-1045
+    of the same sign (f2d_int: the signed zero)."""
     from paper_2604_21438_gb300 import _build
     _build.build()
     L = ctypes.CDLL(_build.BENCH_LIB)
@@ -117,13 +118,19 @@ def test_finite_conversions_match_the_hardware_on_finite_values():
         assert fn(n, p(xf), p(fo), p(fr), p(xd), p(do_), p(dr)) == 0
         outs.append((fo, fr, do_, dr))
     (fo_i, fr, do_i, dr), (fo_f, _, do_f, _) = outs
-    # the finite versions agree with the complete ones bit for bit on finite inputs
-    assert np.array_equal(fo_f.view(np.uint64), fo_i.view(np.uint64))
+    # the finite versions agree with the complete ones bit for bit on finite
+    # inputs, but for f2d of FP32 subnormals
+    normal = (xf == 0) | (np.abs(xf) >= f32.tiny)
+    assert np.array_equal(fo_f[normal].view(np.uint64), fo_i[normal].view(np.uint64))
     assert np.array_equal(do_f.view(np.uint32), do_i.view(np.uint32))
     # and with the hardware on normal numbers and zeros (f2d), outside the ties (d2f)
-    normal = (xf == 0) | (np.abs(xf) >= f32.tiny)
     assert np.array_equal(fo_f[normal].view(np.uint64), fr[normal].view(np.uint64))
-    assert np.all(fo_f[~normal] == 0.0) and np.all(np.signbit(fo_f[~normal]) == np.signbit(xf[~normal]))
+    assert np.all(fo_i[~normal] == 0.0) and np.all(np.signbit(fo_i[~normal]) == np.signbit(xf[~normal]))
+    # f2d_fin of a subnormal m 2^-149: the FP64 subnormal m 2^-1045 of the same sign
+    sub = ~normal
+    m = (xf[sub].view(np.uint32) & np.uint32(0x7fffff)).astype(np.float64)
+    np.testing.assert_array_equal(np.abs(fo_f[sub]), m * 2.0 ** -1045)
+    assert np.all(np.signbit(fo_f[sub]) == np.signbit(xf[sub])) and sub.sum() >= 2
     rest = np.ones(n, bool)
     rest[8:1008] = False
     rest &= ~(np.abs(xd) < f32.tiny) | (xd == 0)
