@@ -41,12 +41,12 @@ YR = inputs.YR
 # profiles/sfchem_li_mixed_gmc256.md, profiles/sfchem_li_fp64_gmc256.md.
 PROFILE_SOURCE = "ncu capture of the GMC-like 256^3 workload, first 512 blocks (profiles/)"
 WORK_PER_SUBSTEP = {
-    "mixed": {"fp32_flops": 1286.8, "fp64_flops": 30.2},
-    "fp64": {"fp32_flops": 1.6, "fp64_flops": 1968.7},
+    "mixed": {"fp32_flops": 1285.2, "fp64_flops": 30.2},
+    "fp64": {"fp32_flops": 1.6, "fp64_flops": 1964.4},
 }
 # DRAM bytes per cell of one solver launch (same captures, 2,097,152 cells:
-# 284.1 MB mixed, 266.0 MB FP64).
-DRAM_BYTES_PER_CELL = {"mixed": 284.14e6 / 2097152, "fp64": 265.98e6 / 2097152}
+# 282.0 MB mixed, 263.7 MB FP64).
+DRAM_BYTES_PER_CELL = {"mixed": 282.03e6 / 2097152, "fp64": 263.72e6 / 2097152}
 # DRAM bytes per cell of the photon kernel (ncu, one launch on the full
 # GMC-like grid: 48.0 B read, 14.7 B written; profiles/sfchem_photon_kernel_gmc256.md)
 PHOTON_DRAM_BYTES_PER_CELL = (805.33e6 + 246.62e6) / 16777216
