@@ -118,6 +118,52 @@ def test_invalid_cells_and_zero_dt():
     z = run_gpu(cells, 0.0, 1.0)
     assert np.all(z["n_sub"] == 0)
     np.testing.assert_array_equal(z["T_g"][ok], cells["T_g"][ok])
+    # outputs of invalid cells are NaN; y_H- of the others is the H- equilibrium
+    # at the final state (formed after the solver), also with nothing to integrate
+    for k in ("y_H", "y_Hp", "y_Hm"):
+        assert np.all(np.isnan(got[k][~ok])) and np.all(np.isnan(z[k][~ok])), k
+    np.testing.assert_allclose(got["y_Hm"][ok], ref["y_Hm"][ok], rtol=1e-9, atol=0)
+    ref0 = oracle.li_step(cells, 0.0, 1.0)
+    np.testing.assert_allclose(z["y_Hm"][ok], ref0["y_Hm"][ok], rtol=1e-9, atol=0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_y_hminus_follows_each_call_in_reused_buffers(precision):
+    """y_H- is formed after the solver from the state the call leaves, in
+    place of the solver's mark (0: advanced, NaN: invalid inputs).  With the
+    same output buffers over three calls, a cell invalid in one call and
+    valid in the next gets its value; the other outputs keep pace."""
+    import torch
+    import paper_2604_21438_gb300 as sf
+    cells = inputs.cells_uniform(96, seed=21)
+    bad = cells["n_H"].copy()
+    bad[[5, 40, 77]] = -1.0
+    s = sf.Solver(precision)
+    d = sf.to_device(cells)
+    pristine = {k: d[k].clone() for k in sf.STATE_FIELDS}
+    got = []
+    for nh in (cells["n_H"], bad, cells["n_H"]):
+        for k in sf.STATE_FIELDS:
+            d[k].copy_(pristine[k])
+        d["n_H"].copy_(torch.as_tensor(nh))
+        s.step(d, 1e3 * YR, 1.0)
+        torch.cuda.synchronize()
+        got.append(sf.to_host({k: d[k] for k in ("y_Hm", "y_H", "T_g", "y_e", "status")}))
+    s.close()
+    ref = oracle.li_step(cells, 1e3 * YR, 1.0)
+    # FP64: the 1e-9 bar; mixed: the stated maximum bound of random cells
+    # (y_H- inherits the errors of y_e and, through k_H2 / k_H3, of T_g)
+    tol = 1e-9 if precision == "fp64" else 5e-3
+    for g in (got[0], got[2]):
+        assert np.all(np.isfinite(g["y_Hm"])) and np.all(g["y_Hm"] > 0)
+        np.testing.assert_allclose(g["y_Hm"], ref["y_Hm"], rtol=tol, atol=0)
+    # the run is deterministic: the third call repeats the first bit for bit
+    for k in ("y_Hm", "y_H", "T_g"):
+        np.testing.assert_array_equal(got[2][k].view(np.uint64), got[0][k].view(np.uint64))
+    inv = np.zeros(96, bool)
+    inv[[5, 40, 77]] = True
+    assert np.all(np.isnan(got[1]["y_Hm"][inv])) and np.all(got[1]["status"][inv] == 2)
+    np.testing.assert_array_equal(got[1]["y_Hm"][~inv].view(np.uint64), got[0]["y_Hm"][~inv].view(np.uint64))
 
 
 @pytest.mark.parametrize("dt_yr,cd", [(1e2, 10.0), (1e3, 1.0), (1e4, 1000.0)])
