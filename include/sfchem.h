@@ -114,7 +114,10 @@ typedef struct sfchem_ctx sfchem_ctx; /* opaque */
  * overwritten; y_H, y_Hp, y_Hm, status, n_sub, n_itr are written when
  * non-NULL.
  * y_H = 1 - 2 y_H2 - y_e and y_Hp = y_e (H-nuclei conservation and charge
- * neutrality, Sec. 2.2.8); y_Hm = k_H2 y_e / k_H3 (H- equilibrium). */
+ * neutrality, Sec. 2.2.8); y_Hm = k_H2 y_e / k_H3 (H- equilibrium, Table 3,
+ * at the final T_gas), formed by a second kernel that each step call queues
+ * on its stream after the solver.  Cells with invalid inputs get NaN in y_H,
+ * y_Hp and y_Hm. */
 typedef struct {
   const double *n_H;   /* H-nuclei number density [cm^-3], > 0 */
   double *T_gas;       /* gas temperature [K] */
@@ -214,7 +217,7 @@ int sfchem_set_config(sfchem_ctx *ctx, const sfchem_config_t *cfg);
  * C_d = cd_factor * 1e4 erg g^-1 K^-1 (> 0).  n_cells == 0 is a no-op (the
  * arrays are not read and may be NULL).
  * Pointers must be 8-byte aligned device pointers (state and fields arrays
- * of n_cells entries).  Asynchronous: returns after the launch. */
+ * of n_cells entries).  Asynchronous: returns once its kernels are queued. */
 int sfchem_step(sfchem_ctx *ctx, const sfchem_state_t *state, const sfchem_fields_t *fields,
                 int64_t n_cells, double dt_seconds, double cd_factor, void *stream);
 
