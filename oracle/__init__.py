@@ -11,7 +11,12 @@ Newton-Raphson backward-Euler reference solver of Sec. 2.2.8.  Parity of the
 stand-in physics (the rates and processes the paper only cites: k_H4, k_H9,
 k_H10, k_H11, photo-heating, photoelectric heating, line cooling and the dust
 opacity) is unpinned against nature: those functions are pinned only through
-closed forms and invariants.
+closed forms and invariants.  Parity unpinned as well: the critical densities
+of k_H7 and of Gamma_1 (their limits are pinned) and the prefactor and He+
+abundance of Lambda_10.
+
+SFCHEM_ORACLE_LIB, when set, names a build of a modified copy of the oracle
+that lib() loads instead of this one (the mutation check of the pins).
 """
 from __future__ import annotations
 
@@ -151,8 +156,15 @@ def lib(fma: bool = False):
             _lib_fma = _setup(ctypes.CDLL(_LIB_FMA))
         return _lib_fma
     if _lib is None:
-        build()
-        _lib = _setup(ctypes.CDLL(_LIB))
+        # SFCHEM_ORACLE_LIB: a build of a modified copy of the oracle, loaded
+        # in place of this one (tests/test_oracle_mutations.py plants a
+        # mistake in such a copy and checks that a pin fails)
+        alt = os.environ.get("SFCHEM_ORACLE_LIB")
+        if alt:
+            _lib = _setup(ctypes.CDLL(os.path.abspath(alt)))
+        else:
+            build()
+            _lib = _setup(ctypes.CDLL(_LIB))
     return _lib
 
 

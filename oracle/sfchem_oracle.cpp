@@ -18,7 +18,11 @@
 // Readings of passages the paper leaves open are marked "reading:"; the
 // stand-ins for physics the paper only cites ("see the reference") are marked
 // "stand-in:".  Stand-in physics is parity unpinned against nature: it is
-// pinned only through the closed forms and invariants of the tests.
+// pinned only through the closed forms and invariants of the tests.  Also
+// parity unpinned, although printed: the critical densities n_cr of k_H7
+// (Table 3) and of Gamma_1 (Table 4) -- their low- and high-density limits
+// are pinned, the position of the transition is not -- and the prefactor and
+// He+ abundance of Lambda_10 (its Boltzmann energy is pinned).
 
 #include "sfchem_oracle.h"
 

@@ -327,3 +327,65 @@ def test_n_cyc_switch_at_300_estimated_subcycles():
             assert len(rec) == 1 and rec[0][1] == dt_h
         else:
             assert rec[0][1] == pytest.approx(dt_h / N_req, rel=1e-13)
+
+
+def test_cosmic_ray_ionization_balanced_by_recombination():
+    """Table 3 H11 and H1 in R_e (Eq. eq_chemq): with only cosmic-ray
+    ionization and radiative recombination, y_e relaxes to the root of
+    k_H11 y_H = k_H1 n_H y_e^2 with y_H = 1 - 2 y_H2 - y_e (y_H2 held), from
+    above and from below.  Catches an ionization or recombination term
+    missing from the electron row, or one with the wrong abundance."""
+    import inputs
+    cfg = oracle.default_config(reaction_mask=(1 << 11) | (1 << 1),
+                                flags=oracle.F_FREEZE_THERMAL | oracle.F_FREEZE_YH2)
+    n, y2 = 1e4, 0.2
+    k = oracle.rates(100.0, 20.0, n, cfg=cfg)
+    a, b, c0 = k[1] * n, k[11], -k[11] * (1.0 - 2.0 * y2)
+    ye_eq = (-b + np.sqrt(b * b - 4.0 * a * c0)) / (2.0 * a)
+    for ye0 in (1e-4, 1e-6):
+        cell = dict(n_H=n, T_g=100.0, T_d=20.0, E_IR=1e4 * C["a_rad"] * 20.0 ** 4, y_H2=y2, y_e=ye0,
+                    G0=0.0, n_EUV=0.0, N_H2=0.0)
+        o = oracle.li_step({kk: np.array([v]) for kk, v in cell.items()}, 1e6 * inputs.YR, 1.0, cfg)
+        assert float(o["y_e"][0]) == pytest.approx(ye_eq, rel=1e-4), ye0
+
+
+def test_three_body_formation_against_the_analytic_solution():
+    """Table 3 H5 in R_H2 (Eq. eq_chemq): three-body formation alone,
+    3H -> H2 + H at k_H5 n(H)^3 per volume, gives dy_H/dt = -2 k_H5 n_H^2
+    y_H^3, solved by 1/y_H^2 = 1/y_H0^2 + 4 k_H5 n_H^2 t.  The LI step, first
+    order in f_chem, approaches it: within 2e-3 at f_chem = 3e-3 (measured
+    6.4e-4), with the error falling about tenfold from f_chem = 3e-2.  k_H5
+    is the printed fit, evaluated here; the powers of n_H and y_H are what
+    is pinned."""
+    import inputs
+    n, T, t = 1e11, 1000.0, 100.0 * inputs.YR
+    k5 = 6e-32 * T ** -0.25 + 2e-31 * T ** -0.5
+    yH_exact = 1.0 / np.sqrt(1.0 + 4.0 * k5 * n * n * t)
+    cell = dict(n_H=n, T_g=T, T_d=T, E_IR=1e4 * C["a_rad"] * T ** 4, y_H2=0.0, y_e=0.0,
+                G0=0.0, n_EUV=0.0, N_H2=0.0)
+    err = {}
+    for fc in (3e-2, 3e-3):
+        cfg = oracle.default_config(reaction_mask=1 << 5, flags=oracle.F_FREEZE_THERMAL | oracle.F_FREEZE_YE,
+                                    f_chem=fc)
+        o = oracle.li_step({kk: np.array([v]) for kk, v in cell.items()}, t, 1.0, cfg)
+        err[fc] = abs(float(o["y_H"][0]) / yH_exact - 1.0)
+    assert err[3e-3] < 2e-3
+    assert 5.0 < err[3e-2] / err[3e-3] < 20.0
+
+
+def test_mass_density_per_h_nucleus_carries_the_helium_mass():
+    """rho = n_H m_H (1 + (m_He/m_H) y_He) (App. C's rho, per H nucleus):
+    y_He is read off the oracle's particle count of neutral atomic gas
+    (n_tot/n_H - 1 from its pressure P = n_tot k_B T) and the helium mass
+    from CODATA (m_He/m_p = 3.97; the oracle's 4 m_H is within 0.2 % in
+    rho).  The helium mass fraction that y_He implies lies in the range of
+    the primordial and protosolar values, Y = 0.24-0.28.  Catches a wrong
+    helium mass or abundance in rho."""
+    n, T = 100.0, 100.0
+    A, b, F, M, ts, aux = oracle.system(n, np.array([0.0, 0.0, T, 20.0, 1e-3]), 0.0, 0.0, 0.0, 1.0, 1.0)
+    rho, P = aux[0], aux[3]
+    y_He = P / (n * C["k_B"] * T) - 1.0
+    mass_ratio = C["m_He"] / C["m_p"]
+    assert rho / (n * C["m_p"]) == pytest.approx(1.0 + mass_ratio * y_He, rel=5e-3)
+    Y = mass_ratio * y_He / (1.0 + mass_ratio * y_He)
+    assert 0.24 <= Y <= 0.28
