@@ -13,7 +13,10 @@ conservation), the dust, IR and gas-grain terms of App. C with their
 Jacobian entries (R_g, T_low, gamma_d, zeta, beta_d, beta_IR, kappa, the
 emission law), the gas state (particle count, helium mass in rho,
 Eq. ap_eq:alpha_g), and the controller of Sec. 2.2.8 (f_chem, N_cyc, the
-(gamma - 1) of Eq. timescale_energy, C_d in the dust timescale).
+(gamma - 1) of Eq. timescale_energy, C_d in the dust timescale); and, against
+its own pin file, the photon consumption after the update (reading R32:
+absorbers, shielding, unit conversions, the implicit decay on both sides of
+lam dt = 1, the split of the removed photons).
 
 Not covered, because nothing independent of the printed formula pins them
 (parity unpinned): the critical densities n_cr of k_H7 and of Gamma_1 (only
@@ -31,6 +34,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "sfchem_oracle.cpp")
 HDR = os.path.join(ROOT, "oracle", "sfchem_oracle.h")
 PINS = [os.path.join(ROOT, "tests", f) for f in ("test_oracle_pins.py", "test_oracle_pins_physics.py")]
+PHOTON_PINS = [os.path.join(ROOT, "tests", "test_oracle_photon.py")]
 
 # (name, text of the oracle, replacement): one change each
 MUTATIONS = [
@@ -100,7 +104,27 @@ MUTATIONS = [
 ]
 
 
-def _build_and_run(work, name, old, new):
+# the photon consumption after the update (reading R32 of Sec. 2.2.8)
+PHOTON_MUTATIONS = [
+    ("EUV absorption by H without y_H", "c_light * nh * sigma_EUV * yH;", "c_light * nh * sigma_EUV;"),
+    ("EUV dust absorption dropped", "const double xE = (lam_H + lam_dE) * dt[i];", "const double xE = (lam_H) * dt[i];"),
+    ("EUV opaque branch n/(1 + 2x)", "const double nE = xE < 1.0 ? n_EUV[i] - takeE : n_EUV[i] / (1.0 + xE);",
+     "const double nE = xE < 1.0 ? n_EUV[i] - takeE : n_EUV[i] / (1.0 + 2.0 * xE);"),
+    ("EUV thin branch explicit (n x instead of n x/(1+x))", "n_EUV[i] * (xE / (1.0 + xE))", "n_EUV[i] * (xE)"),
+    ("FUV self-shielding dropped", "const double lam_2 = k_LW * fsh * nh", "const double lam_2 = k_LW * nh"),
+    ("FUV photon energy ratio inverted", "y_H2[i] * hnu_FUV / u_Habing;", "y_H2[i] * u_Habing / hnu_FUV;"),
+    ("FUV absorbed by y_H instead of y_H2", "nh * y_H2[i] * hnu_FUV", "nh * yH * hnu_FUV"),
+    ("FUV opaque branch G0/x", "const double g = xF < 1.0 ? G0[i] - takeF : G0[i] / (1.0 + xF);",
+     "const double g = xF < 1.0 ? G0[i] - takeF : G0[i] / (xF);"),
+    ("EUV split between H and dust swapped", "absorbed[4 * i + 0] = sE > 0.0 ? dE * lam_H / sE : 0.0;",
+     "absorbed[4 * i + 0] = sE > 0.0 ? dE * lam_dE / sE : 0.0;"),
+    ("FUV photons removed not converted from G0 units", "const double dF = takeF * u_Habing / hnu_FUV;",
+     "const double dF = takeF;"),
+    ("y_H without y_e", "std::max(1.0 - 2.0 * y_H2[i] - y_e[i], 0.0);", "std::max(1.0 - 2.0 * y_H2[i], 0.0);"),
+]
+
+
+def _build_and_run(work, name, old, new, pins=PINS):
     """Build the (mutated) copy in `work` and run the pins against it;
     returns (pins passed?, pytest's last line)."""
     src = open(SRC).read()
@@ -118,18 +142,26 @@ def _build_and_run(work, name, old, new):
                     "sfchem_oracle.cpp"], cwd=d, check=True, capture_output=True)
     env = dict(os.environ, SFCHEM_ORACLE_LIB=so, OMP_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "not gpu", "-p", "no:cacheprovider",
-                        *PINS], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+                        *pins], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     lines = [l for l in r.stdout.splitlines() if l.strip()]
     return r.returncode == 0, (lines[-1] if lines else r.stderr[-300:])
 
 
-def test_every_mutation_of_the_printed_physics_fails_a_pin():
-    cases = [("unmodified", None, None)] + MUTATIONS
+def _check(mutations, pins):
+    cases = [("unmodified", None, None)] + mutations
     with tempfile.TemporaryDirectory() as work, cf.ThreadPoolExecutor(min(8, os.cpu_count() or 1)) as ex:
-        res = dict(zip([c[0] for c in cases], ex.map(lambda c: _build_and_run(work, *c), cases)))
+        res = dict(zip([c[0] for c in cases], ex.map(lambda c: _build_and_run(work, *c, pins=pins), cases)))
     ok, last = res.pop("unmodified")
     assert ok, f"the unmodified oracle copy fails its pins: {last}"
     survivors = {name: last for name, (passed, last) in res.items() if passed}
     for name, (passed, last) in res.items():
         print(f"{name}: {'SURVIVED' if passed else 'caught'} ({last})")
     assert not survivors, f"mutations that no pin catches: {survivors}"
+
+
+def test_every_mutation_of_the_printed_physics_fails_a_pin():
+    _check(MUTATIONS, PINS)
+
+
+def test_every_mutation_of_the_photon_update_fails_a_pin():
+    _check(PHOTON_MUTATIONS, PHOTON_PINS)

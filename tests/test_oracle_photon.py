@@ -104,3 +104,31 @@ def test_photons_absorbed_by_dust_carry_the_dust_row_uv_energy():
     energy = r["absorbed"][0, 1] * HNU_EUV + r["absorbed"][0, 3] * oracle.HNU_FUV
     lam_dt = 1.0 - r["G0"][0] / cell["G0"]
     assert energy == pytest.approx(rho * EUV * dt, rel=5 * lam_dt + 1e-9)
+
+
+def test_each_band_decays_implicitly_at_its_thin_limit_rate():
+    """Reading R32: over a step each band keeps n / (1 + lam dt) of its
+    photons (the implicit update of dn/dt = -lam n), on both sides of
+    lam dt = 1 (the thin and opaque formulas).  lam is measured from the
+    oracle itself in the thin limit (photons removed / (n dt), per cell at
+    lam dt ~ 1e-7, where the form of the update changes it by ~1e-7), so the
+    pin fixes the form of the update, not its stand-in constants: an
+    explicit thin-side update (n (1 - lam dt)) or a mismatch between the two
+    branches fails it."""
+    c = _cells(64, seed=5)
+
+    def thin_rate(key):
+        dt = np.full(len(c["n_H"]), 1e-3)
+        for _ in range(2):           # a rough rate, then dt = 1e-7 / rate per cell
+            r = oracle.photon_update(c, dt)
+            lam = (c[key] - r[key]) / (c[key] * dt)
+            dt = 1e-7 / lam
+        return lam
+
+    lam_E, lam_F = thin_rate("n_EUV"), thin_rate("G0")
+    assert np.all(lam_E > 0) and np.all(lam_F > 0)
+    for x in (0.3, 0.999, 1.001, 4.0):
+        rE = oracle.photon_update(c, x / lam_E)
+        np.testing.assert_allclose(rE["n_EUV"], c["n_EUV"] / (1.0 + x), rtol=1e-6)
+        rF = oracle.photon_update(c, x / lam_F)
+        np.testing.assert_allclose(rF["G0"], c["G0"] / (1.0 + x), rtol=1e-6)
