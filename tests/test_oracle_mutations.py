@@ -18,10 +18,16 @@ its own pin file, the photon consumption after the update (reading R32:
 absorbers, shielding, unit conversions, the implicit decay on both sides of
 lam dt = 1, the split of the removed photons).
 
+The Newton-Raphson reference is covered too: its residuals, its stopping
+tolerance, the coverage of dt_hydro by its substeps and its outer T_g step.
+
 Not covered, because nothing independent of the printed formula pins them
 (parity unpinned): the critical densities n_cr of k_H7 and of Gamma_1 (only
 their limits are pinned), the prefactor and He+ abundance of Lambda_10, and
-the stand-ins for the rates and processes the paper only cites."""
+the stand-ins for the rates and processes the paper only cites.  Not
+covered either: an error in a Newton matrix (it changes the iterations, not
+the root they converge to) and the tolerance relaxed to 1e-3 after
+N_itr,limit/2 outer iterations (no pin's cell takes that many)."""
 import concurrent.futures as cf
 import os
 import subprocess
@@ -101,6 +107,16 @@ MUTATIONS = [
     ("rho: helium mass 4 m_H -> m_H", "ci.rho = (1.0 + 4.0 * y_He) * mH * n;", "ci.rho = (1.0 + y_He) * mH * n;"),
     ("f_chem 0.03 -> 0.3", "c->f_chem = 0.03;", "c->f_chem = 0.3;"),
     ("dust timescale without C_d", "ratio_ts(u[3], d.D / Cd)", "ratio_ts(u[3], d.D)"),
+    # the Newton-Raphson reference (Sec. 2.2.8)
+    ("NR species residual with dt/2", "real G[2] = {u[0] - u0[0] - dt * RH2.v, u[1] - u0[1] - dt * Re.v};",
+     "real G[2] = {u[0] - u0[0] - 0.5 * dt * RH2.v, u[1] - u0[1] - dt * Re.v};"),
+    ("NR energy residual without gas-grain", "g = gs0.alpha_g * (Tg - u0[2]) - dt * (net.v / ci.rho + d.Qgg);",
+     "g = gs0.alpha_g * (Tg - u0[2]) - dt * (net.v / ci.rho);"),
+    ("NR energy residual with 2 dt", "g = gs0.alpha_g * (Tg - u0[2]) - dt * (net.v / ci.rho + d.Qgg);",
+     "g = gs0.alpha_g * (Tg - u0[2]) - 2.0 * dt * (net.v / ci.rho + d.Qgg);"),
+    ("NR tolerance 1e-5 -> 1e-2", "c->nr_tol = 1e-5;", "c->nr_tol = 1e-2;"),
+    ("NR substeps: time double-counted", "t = (i == 0) ? dt_h : t + dts;", "t = (i == 0) ? dt_h : t + 2.0 * dts;"),
+    ("NR outer step sign and length", "real Tn = std::max(Tg - g / dg, T_CMB);", "real Tn = std::max(Tg + 0.5 * g / dg, T_CMB);"),
 ]
 
 

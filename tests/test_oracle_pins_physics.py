@@ -389,3 +389,52 @@ def test_mass_density_per_h_nucleus_carries_the_helium_mass():
     assert rho / (n * C["m_p"]) == pytest.approx(1.0 + mass_ratio * y_He, rel=5e-3)
     Y = mass_ratio * y_He / (1.0 + mass_ratio * y_He)
     assert 0.24 <= Y <= 0.28
+
+
+def _three_body_cell(n, T):
+    return dict(n_H=n, T_g=T, T_d=T, E_IR=1e4 * C["a_rad"] * T ** 4, y_H2=0.0, y_e=0.0,
+                G0=0.0, n_EUV=0.0, N_H2=0.0)
+
+
+def test_nr_step_is_the_backward_euler_root():
+    """The Newton-Raphson reference of Sec. 2.2.8 solves the backward-Euler
+    equations of the step: with three-body formation alone (Table 3 H5;
+    temperatures and electrons held), y_H' + 2 dt k_H5 n_H^2 y_H'^3 = y_H0,
+    a cubic with one positive root (numpy).  One Newton-Raphson step over
+    dt_hydro lands on it to 1e-10 (the 1e-5 stopping test and quadratic
+    convergence).  Catches a wrong residual or a wrong dt in it."""
+    n, T = 1e11, 1000.0
+    k5 = 6e-32 * T ** -0.25 + 2e-31 * T ** -0.5
+    cfg = oracle.default_config(reaction_mask=1 << 5, flags=oracle.F_FREEZE_THERMAL | oracle.F_FREEZE_YE)
+    one = {k: np.array([v]) for k, v in _three_body_cell(n, T).items()}
+    import inputs
+    for dt_yr in (10.0, 100.0, 1000.0):
+        dt = dt_yr * inputs.YR
+        o = oracle.nr_step(one, dt, 1.0, cfg)
+        assert o["n_sub"][0] == 1 and o["status"][0] == 0
+        yH = 1.0 - 2.0 * o["y_H2"][0] - o["y_e"][0]
+        r = np.roots([2.0 * dt * k5 * n * n, 0.0, 1.0, -1.0])
+        r = r[np.abs(r.imag) < 1e-12].real
+        root = r[r > 0][0]
+        assert yH == pytest.approx(root, rel=1e-10), dt_yr
+
+
+def test_nr_substeps_cover_the_hydro_step():
+    """Sec. 2.2.8's substepping of the Newton-Raphson reference: when an
+    attempt fails, dt_sub = (dt_hydro - t_sub) / 2^i, and the accepted
+    substeps must add up to dt_hydro.  With the iteration limit at 2 the
+    100-yr step of three-body formation cannot be taken at once (its one
+    backward-Euler step would be 19 % off the analytic y_H): the reference
+    subdivides and, being first order in the substep, ends within 1 % of the
+    analytic solution 1/y_H^2 = 1 + 4 k_H5 n_H^2 t (measured 0.4 %).  Time
+    lost or double-counted between substeps fails it."""
+    import inputs
+    n, T = 1e11, 1000.0
+    k5 = 6e-32 * T ** -0.25 + 2e-31 * T ** -0.5
+    dt = 100.0 * inputs.YR
+    cfg = oracle.default_config(reaction_mask=1 << 5, flags=oracle.F_FREEZE_THERMAL | oracle.F_FREEZE_YE,
+                                nr_itr_limit=2)
+    o = oracle.nr_step({k: np.array([v]) for k, v in _three_body_cell(n, T).items()}, dt, 1.0, cfg)
+    assert o["status"][0] == 0 and o["n_sub"][0] > 10
+    yH = 1.0 - 2.0 * o["y_H2"][0] - o["y_e"][0]
+    assert yH == pytest.approx(1.0 / np.sqrt(1.0 + 4.0 * k5 * n * n * dt), rel=1e-2)
