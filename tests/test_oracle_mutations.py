@@ -12,8 +12,12 @@ k_H7, k_H8) and Table 4 (Gamma_1, Lambda_5-Lambda_12), the rate equations
 conservation), the dust, IR and gas-grain terms of App. C with their
 Jacobian entries (R_g, T_low, gamma_d, zeta, beta_d, beta_IR, kappa, the
 emission law), the gas state (particle count, helium mass in rho,
-Eq. ap_eq:alpha_g), and the controller of Sec. 2.2.8 (f_chem, N_cyc, the
-(gamma - 1) of Eq. timescale_energy, C_d in the dust timescale); and, against
+Eq. ap_eq:alpha_g), the controller and update of Sec. 2.2.8 (f_chem,
+y_floor, N_cyc, the (gamma - 1) and the gas-grain term of Eq.
+timescale_energy, C_d in the dust timescale, the dust timescale dropped in
+tight coupling, the truncation of the last substep, the time accounting,
+M - dt J and its heat capacities, the step-rejection bounds, the projection
+and the E_IR floor); and, against
 its own pin file, the photon consumption after the update (reading R32:
 absorbers, shielding, unit conversions, the implicit decay on both sides of
 lam dt = 1, the split of the removed photons).
@@ -39,7 +43,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "sfchem_oracle.cpp")
 HDR = os.path.join(ROOT, "oracle", "sfchem_oracle.h")
-PINS = [os.path.join(ROOT, "tests", f) for f in ("test_oracle_pins.py", "test_oracle_pins_physics.py")]
+# (the physics pins first: a mutant that slows the LI step down fails one of
+# them before the longer integrations of the other file run)
+PINS = [os.path.join(ROOT, "tests", f) for f in ("test_oracle_pins_physics.py", "test_oracle_pins.py")]
 PHOTON_PINS = [os.path.join(ROOT, "tests", "test_oracle_photon.py")]
 
 # (name, text of the oracle, replacement): one change each
@@ -107,6 +113,27 @@ MUTATIONS = [
     ("rho: helium mass 4 m_H -> m_H", "ci.rho = (1.0 + 4.0 * y_He) * mH * n;", "ci.rho = (1.0 + y_He) * mH * n;"),
     ("f_chem 0.03 -> 0.3", "c->f_chem = 0.03;", "c->f_chem = 0.3;"),
     ("dust timescale without C_d", "ratio_ts(u[3], d.D / Cd)", "ratio_ts(u[3], d.D)"),
+    ("energy timescale without the gas-grain term", "real GmL = ci.rho * (q.v + d.Qgg);", "real GmL = ci.rho * (q.v);"),
+    ("step rejection: y_H2 bound 0.5 -> 5", "bool small = std::fabs(du[0]) <= 0.5 * std::max(u0[0], c.y_floor) &&",
+     "bool small = std::fabs(du[0]) <= 5.0 * std::max(u0[0], c.y_floor) &&"),
+    ("step rejection: y_e bound 0.5 -> 5", "std::fabs(du[1]) <= 0.5 * std::max(u0[1], c.y_floor) &&",
+     "std::fabs(du[1]) <= 5.0 * std::max(u0[1], c.y_floor) &&"),
+    ("step rejection: T_g factor 2 -> 10", "du[2] <= u0[2] && du[2] >= -0.5 * u0[2];", "du[2] <= 9.0 * u0[2] && du[2] >= -0.9 * u0[2];"),
+    ("projection y_H2 <= 1 - y_e", "u[0] = std::min(std::max(u[0], 0.0), (1.0 - u[1]) / 2.0);",
+     "u[0] = std::min(std::max(u[0], 0.0), (1.0 - u[1]));"),
+    ("projection without y_e <= 1", "u[1] = std::min(std::max(u[1], 0.0), 1.0);", "u[1] = std::max(u[1], 0.0);"),
+    ("E_IR floor from T_CMB^3", "real E_floor_of() { return (c_light / c_red) * a_rad * std::pow(T_CMB, 4); }",
+     "real E_floor_of() { return (c_light / c_red) * a_rad * std::pow(T_CMB, 3); }"),
+    ("last substep not truncated to the time left", "if (dtc >= rem || rem - dtc <= 1e-12 * dt_h) { dts = rem; last = true; }",
+     "if (dtc >= rem || rem - dtc <= 1e-12 * dt_h) { dts = dtc; last = true; }"),
+    ("time advanced by 2 dt_s", "t = last ? dt_h : t + dts;", "t = last ? dt_h : t + 2.0 * dts;"),
+    ("tight mode keeps the dust timescale", "if (!tight) tmin = std::min(tmin, s.ts[0]);", "tmin = std::min(tmin, s.ts[0]);"),
+    ("update u += 2 du", "for (int j = 0; j < 5; ++j) u[j] += du[j];", "for (int j = 0; j < 5; ++j) u[j] += 2.0 * du[j];"),
+    ("heat capacity alpha_g missing from M", "s.M[2] = gs.alpha_g;", "s.M[2] = 1.0;"),
+    ("C_d missing from M", "s.M[3] = Cd;", "s.M[3] = 1.0;"),
+    ("A = M + dt J", "A[r * 5 + j] = (r == j ? s.M[r] : 0.0) - dt * s.J[r][j];",
+     "A[r * 5 + j] = (r == j ? s.M[r] : 0.0) + dt * s.J[r][j];"),
+    ("y_floor 1e-8 -> 1e-4", "c->y_floor = 1e-8;", "c->y_floor = 1e-4;"),
     # the Newton-Raphson reference (Sec. 2.2.8)
     ("NR species residual with dt/2", "real G[2] = {u[0] - u0[0] - dt * RH2.v, u[1] - u0[1] - dt * Re.v};",
      "real G[2] = {u[0] - u0[0] - 0.5 * dt * RH2.v, u[1] - u0[1] - dt * Re.v};"),

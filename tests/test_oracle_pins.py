@@ -110,10 +110,14 @@ def test_case1_discrete_closed_form():
         # controller: dt_s = f_chem * y / R (except the truncated last substep)
         R = k8 * g["case1_n_H"] * (1.0 - 2.0 * prev - cell["y_e"])
         if t_end < 2e5 * YR:
-            assert dts == pytest.approx(0.03 * prev / R, rel=1e-13)
-        assert yH2 == pytest.approx(yeq + (prev - yeq) / (1.0 + lam * dts), rel=1e-14)
-        y = yeq + (y - yeq) / (1.0 + lam * dts)
-        assert yH2 == pytest.approx(y, rel=1e-11)
+            assert dts == pytest.approx(0.03 * prev / R, rel=1e-13, abs=0)
+        # the same update written as an increment, (y_eq - y) x / (1 + x): the
+        # form y_eq + (y - y_eq) / (1 + x) cancels from ~0.5 down to y ~ 1e-5
+        # and would carry 5e-12 of its own rounding
+        x = lam * dts
+        assert yH2 == pytest.approx(prev + (yeq - prev) * (x / (1.0 + x)), rel=1e-14, abs=0)
+        y = y + (yeq - y) * (x / (1.0 + x))
+        assert yH2 == pytest.approx(y, rel=1e-11, abs=0)
         assert ye == cell["y_e"] and Tg == cell["T_g"] and Td == cell["T_d"]
         prev = yH2
 
@@ -165,14 +169,15 @@ def test_case2_discrete_closed_form_and_analytic():
                                 flags=oracle.F_FREEZE_THERMAL | oracle.F_FREEZE_YH2)
     rec, st = oracle.li_trace(cell, 1.0 * YR, 1.0, cfg)
     R = oracle.rates(12000.0, 75.0, 100.0, 0.0, cell["n_EUV"], 0.0, cfg)[9]
-    assert R == pytest.approx(g["case2_R_ph"], rel=1e-12)
+    assert R == pytest.approx(g["case2_R_ph"], rel=1e-12, abs=0)
     yeq = 1.0 - 2.0 * cell["y_H2"]
     y = cell["y_e"]
     prev = cell["y_e"]
     for t_end, dts, yH2, ye, *_ in rec:
-        assert ye == pytest.approx(yeq + (prev - yeq) / (1.0 + R * dts), rel=1e-14)
-        y = yeq + (y - yeq) / (1.0 + R * dts)
-        assert ye == pytest.approx(y, rel=1e-11)
+        x = R * dts            # the update as an increment (see P1)
+        assert ye == pytest.approx(prev + (yeq - prev) * (x / (1.0 + x)), rel=1e-14, abs=0)
+        y = y + (yeq - y) * (x / (1.0 + x))
+        assert ye == pytest.approx(y, rel=1e-11, abs=0)
         prev = ye
     t = rec[:, 0]
     exact = 1.0 + (g["case2_y_Hp"] - 1.0) * np.exp(-R * t)           # Eq. HIIform2
@@ -203,7 +208,7 @@ def test_case2_ionization_recombination_equilibrium():
     ye = (-b + np.sqrt(b * b - 4 * a * c0)) / (2 * a)
     # the LI step ends with one linearized step toward the balance, so the
     # neutral fraction agrees with the exact root to a fraction of a per cent
-    assert float(o["y_H"][0]) == pytest.approx(1.0 - 2.0 * cell["y_H2"] - ye, rel=5e-3)
+    assert float(o["y_H"][0]) == pytest.approx(1.0 - 2.0 * cell["y_H2"] - ye, rel=5e-3, abs=0)
 
 
 def test_h2_formation_dissociation_equilibrium():
@@ -214,7 +219,7 @@ def test_h2_formation_dissociation_equilibrium():
     o = oracle.li_step({k: np.array([v]) for k, v in cell.items()}, 1e7 * YR, 1.0, cfg)
     k = oracle.rates(50.0, 15.0, 300.0, 3.0, 0.0, 1e15, cfg)
     yeq = k[8] * 300.0 * (1.0 - 1e-4) / (2.0 * k[8] * 300.0 + k[10])
-    assert float(o["y_H2"][0]) == pytest.approx(yeq, rel=1e-10)
+    assert float(o["y_H2"][0]) == pytest.approx(yeq, rel=1e-10, abs=0)
 
 
 def test_radiative_balance_dust_temperature():
@@ -233,7 +238,7 @@ def test_radiative_balance_dust_temperature():
     EUV = oracle.system(10.0, u, 30.0, 0.0, 1e14, 1.0, 1.0, cfg)[5][2]
     Teq = (EUV * 10.0 ** 2 / (0.1 * 7.565733250e-15 * 2.99792458e10)) ** (1.0 / 6.0)
     assert Teq < 200.0
-    assert float(o["T_d"][0]) == pytest.approx(Teq, rel=1e-10)
+    assert float(o["T_d"][0]) == pytest.approx(Teq, rel=1e-10, abs=0)
 
 
 def test_conservation_and_bounds():
@@ -483,3 +488,108 @@ def test_step_rejection_keeps_updates_small():
         finals.append(rec[-1][4])
         assert 10.0 < rec[-1][4] < 2e4
     assert abs(finals[0] / finals[1] - 1.0) < 1e-3
+
+
+def test_step_rejection_bounds_on_wide_range_cells():
+    """The same reading on the wide-range cells, where it fires (about 7 %
+    of them take at least one halving): on every cell that had a substep
+    redone, every accepted update keeps |dy_H2|, |dy_e| <= max(y, y_floor)/2
+    and T_g within a factor 2, and the controller as printed
+    (ORACLE_F_NO_REJECT) takes updates outside those bounds on the same
+    cells, so the bounds are what the halving enforces."""
+    c = inputs.cells_extreme(4096, seed=3)
+    o = oracle.li_step(c, 1e3 * YR, 1.0)
+    picks = np.nonzero(o["n_rej"] > 0)[0][:24]
+    assert len(picks) == 24
+    cfg = oracle.default_config()
+    lit = oracle.default_config(flags=oracle.F_NO_REJECT)
+    outside = 0
+    for i in picks:
+        cell = {k: float(c[k][i]) for k in inputs.FIELDS}
+        for conf, bounded in ((cfg, True), (lit, False)):
+            rec, st = oracle.li_trace(cell, 1e3 * YR, 1.0, conf)
+            u = np.array([[cell["y_H2"], cell["y_e"], cell["T_g"]]] + [r[2:5] for r in rec])
+            dy = np.abs(np.diff(u[:, :2], axis=0))
+            ok_y = dy <= 0.5 * np.maximum(u[:-1, :2], conf.y_floor) * (1 + 1e-12)
+            ratio = u[1:, 2] / u[:-1, 2]
+            ok_T = (ratio <= 2.0 + 1e-12) & (ratio >= 0.5 - 1e-12)
+            if bounded:
+                assert np.all(ok_y) and np.all(ok_T), i
+            else:
+                outside += int(not (np.all(ok_y) and np.all(ok_T)))
+    assert outside >= len(picks) // 2
+
+
+def test_conservation_and_bounds_on_wide_range_cells():
+    """P6 where the bounds bind: on the wide-range cells (y_e within 1e-8 of 1
+    for a fifth of them, y_H2 within 1e-8 of (1 - y_e)/2 for 30 %), after the
+    step y_H + 2 y_H2 + y_H+ = 1 with every abundance in [0, 1], both
+    temperatures at least T_CMB (Fixsen 2009) and E_IR at least the CMB's
+    energy density seen through the reduced light speed, (c / c~) a T_CMB^4
+    with c~ = 1e-4 c (Sec. 2) and a from CODATA."""
+    g = golden("physical_constants.txt")
+    c = inputs.cells_extreme(4096, seed=3)
+    o = oracle.li_step(c, 1e3 * YR, 1.0)
+    ok = (o["status"] & oracle.ST_BADINPUT) == 0
+    assert ok.mean() > 0.99
+    np.testing.assert_allclose((o["y_H"] + 2 * o["y_H2"] + o["y_Hp"])[ok], 1.0, rtol=0, atol=1e-15)
+    for k in ("y_H", "y_H2", "y_e"):
+        assert np.all((o[k][ok] >= 0) & (o[k][ok] <= 1)), k
+    T_cmb = g["T_CMB"]
+    assert np.all(o["T_g"][ok] >= T_cmb * (1 - 1e-4)) and np.all(o["T_d"][ok] >= T_cmb * (1 - 1e-4))
+    E_floor = 1e4 * g["a_rad"] * T_cmb ** 4
+    assert np.all(o["E_IR"][ok] >= E_floor * (1 - 1e-3))
+    # where it binds: an E_IR below the floor, drained further by dust held at
+    # 10 K that absorbs IR and does not emit, ends at the floor
+    cfg = oracle.default_config(process_mask=oracle.P_DUST_IRABS, reaction_mask=0,
+                                flags=oracle.F_FREEZE_TG | oracle.F_FREEZE_TD | oracle.F_FREEZE_YH2
+                                | oracle.F_FREEZE_YE)
+    cell = one_cell(n_H=1e4, T_g=10.0, T_d=10.0, E_IR=1e-12)
+    r = oracle.li_step({k: np.array([v]) for k, v in cell.items()}, 1.0 * YR, 1.0, cfg)
+    assert float(r["E_IR"][0]) == pytest.approx(E_floor, rel=1e-3, abs=0)
+
+
+def test_projection_of_inputs_at_the_budget_tolerance():
+    """The projection of Sec. 2.2.8 (H-nuclei conservation, y_H >= 0) applies
+    to the inputs: a state with 2 y_H2 + y_e = 1 + 5e-10 (accepted: the
+    input check allows 1e-9) leaves the call with y_H2 = (1 - y_e)/2, y_H = 0
+    and y_H + 2 y_H2 + y_H+ = 1, also with nothing to integrate."""
+    ye = 0.25
+    cell = one_cell(y_e=ye, y_H2=(1.0 - ye) / 2.0 + 2.5e-10)
+    for dt in (0.0, 1.0 * YR):
+        o = oracle.li_step({k: np.array([v]) for k, v in cell.items()}, dt, 1.0,
+                           oracle.default_config(reaction_mask=0, flags=oracle.F_FREEZE_THERMAL))
+        assert o["status"][0] & oracle.ST_BADINPUT == 0
+        assert o["y_H2"][0] == (1.0 - ye) / 2.0 and o["y_H"][0] == 0.0
+        assert o["y_H"][0] + 2.0 * o["y_H2"][0] + o["y_Hp"][0] == 1.0
+
+
+def test_projection_bounds_a_linearized_overshoot():
+    """The LI update is linear in the change: collisional ionization (Table 3
+    H0) at y_e = 0.8, T_g = 1e5 K has dR_e/dy_e = k_H0 n (y_H - y_e) < 0, and
+    one long substep (f_chem = 10) carries y_e to 0.8 + 0.16/0.6 = 1.07 > 1
+    (within the step-rejection bound of 0.4).  The projection keeps y_e <= 1
+    and y_H >= 0."""
+    cfg = oracle.default_config(reaction_mask=1 << 0, flags=oracle.F_FREEZE_THERMAL | oracle.F_FREEZE_YH2,
+                                f_chem=10.0)
+    cell = one_cell(n_H=1.0, T_g=1e5, y_H2=0.0, y_e=0.8, G0=0.0)
+    rec, st = oracle.li_trace(cell, 1e10, 1.0, cfg)
+    assert len(rec) == 1 and rec[0][3] == 1.0
+    o = oracle.li_step({k: np.array([v]) for k, v in cell.items()}, 1e10, 1.0, cfg)
+    assert o["y_e"][0] == 1.0 and o["y_H"][0] == 0.0
+
+
+def test_step_rejection_bounds_the_gas_temperature():
+    """The T_g bound of the step-rejection reading: photoelectric heating
+    alone (independent of T_g) with f_chem = 10 would multiply T_g by ~11 in
+    one substep; every recorded substep stays within a factor 2 (measured
+    1.71), after halvings."""
+    cfg = oracle.default_config(reaction_mask=0, process_mask=oracle.P_G4_PHOTOELEC,
+                                flags=oracle.F_FREEZE_TD | oracle.F_FREEZE_EIR | oracle.F_FREEZE_YH2
+                                | oracle.F_FREEZE_YE, f_chem=10.0)
+    cell = one_cell(n_H=1.0, T_g=100.0, y_H2=0.0, y_e=1e-4, G0=10.0)
+    rec, st = oracle.li_trace(cell, 1e5 * YR, 1.0, cfg)
+    T = np.array([cell["T_g"]] + [r[4] for r in rec])
+    assert np.all(T[1:] / T[:-1] <= 2.0 + 1e-12)
+    o = oracle.li_step({k: np.array([v]) for k, v in cell.items()}, 1e5 * YR, 1.0, cfg)
+    assert o["n_halv"][0] > 0
