@@ -11,7 +11,8 @@ Newton-Raphson backward-Euler reference solver of Sec. 2.2.8.  Parity of the
 stand-in physics (the rates and processes the paper only cites: k_H4, k_H9,
 k_H10, k_H11, photo-heating, photoelectric heating, line cooling and the dust
 opacity) is unpinned against nature: those functions are pinned only through
-closed forms and invariants.  Parity unpinned as well: the critical densities
+closed forms and invariants (the line cooling's LTE limit excepted, which is
+pinned to atomic data).  Parity unpinned as well: the critical densities
 of k_H7 and of Gamma_1 (their limits are pinned) and the prefactor and He+
 abundance of Lambda_10.
 

@@ -18,7 +18,8 @@
 // Readings of passages the paper leaves open are marked "reading:"; the
 // stand-ins for physics the paper only cites ("see the reference") are marked
 // "stand-in:".  Stand-in physics is parity unpinned against nature: it is
-// pinned only through the closed forms and invariants of the tests.  Also
+// pinned only through the closed forms and invariants of the tests (the LTE
+// limit of the line-cooling stand-in excepted, pinned to atomic data).  Also
 // parity unpinned, although printed: the critical densities n_cr of k_H7
 // (Table 3) and of Gamma_1 (Table 4) -- their low- and high-density limits
 // are pinned, the position of the transition is not -- and the prefactor and

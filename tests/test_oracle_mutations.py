@@ -28,7 +28,8 @@ tolerance, the coverage of dt_hydro by its substeps and its outer T_g step.
 Not covered, because nothing independent of the printed formula pins them
 (parity unpinned): the critical densities n_cr of k_H7 and of Gamma_1 (only
 their limits are pinned), the prefactor and He+ abundance of Lambda_10, and
-the stand-ins for the rates and processes the paper only cites.  Not
+the stand-ins for the rates and processes the paper only cites -- except
+the line cooling, whose LTE limit is pinned to atomic data.  Not
 covered either: an error in a Newton matrix (it changes the iterations, not
 the root they converge to) and the tolerance relaxed to 1e-3 after
 N_itr,limit/2 outer iterations (no pin's cell takes that many)."""
@@ -70,6 +71,11 @@ MUTATIONS = [
     ("(gamma - 1) dropped from dt_energy", "gs.P / ((c.gamma_ad - 1.0) * std::fabs(GmL))", "gs.P / (std::fabs(GmL))"),
     ("(gamma - 1) dropped from alpha_g", "kB / ((c.gamma_ad - 1.0) * s.mu * mH)", "kB / (s.mu * mH)"),
     ("N_cyc /10", "c->n_cyc = 300;", "c->n_cyc = 30;"),
+    # the line-cooling stand-in (reading R23), pinned at LTE to atomic data
+    ("[C II] excitation temperature 91.2 K -> 9.12 K", "TC_star = 91.2,", "TC_star = 9.12,"),
+    ("[O I] A x10", "A_O = 8.9e-5,", "A_O = 8.9e-4,"),
+    ("[O I] statistical weight ratio 3/5 -> 5/3", "g_O = 0.6,", "g_O = 1.6667,"),
+    ("[C II] abundance x10", "const double x_C = 1.4e-4,", "const double x_C = 1.4e-3,"),
     # other printed rates
     ("k_H0 slope 13.536556 -> 13.636556", "-32.71396786, 13.536556,", "-32.71396786, 13.636556,"),
     ("k_H1 x10", "k[1] = 2.753e-14", "k[1] = 2.753e-13"),

@@ -438,3 +438,30 @@ def test_nr_substeps_cover_the_hydro_step():
     assert o["status"][0] == 0 and o["n_sub"][0] > 10
     yH = 1.0 - 2.0 * o["y_H2"][0] - o["y_e"][0]
     assert yH == pytest.approx(1.0 / np.sqrt(1.0 + 4.0 * k5 * n * n * dt), rel=1e-2, abs=0)
+
+
+def test_line_cooling_stand_in_at_lte():
+    """Reading R23 (line cooling, a stand-in for the cited models): two-level
+    [C II] 158 um and [O I] 63 um emitters at fixed abundances.  Above their
+    critical densities the level populations are Boltzmann, and each line
+    cools at x f_d n_H h nu A g e^{-h nu / k T} / (1 + g e^{-h nu / k T}),
+    whatever the collision rates.  The oracle's line cooling at n_H = 1e10
+    (three decades above either critical density) matches that sum built
+    from laboratory wavelengths, NIST A values, statistical weights and
+    diffuse-cloud gas-phase abundances (tests/golden/fine_structure_lines.txt)
+    within 2 %, at 30, 100 and 1000 K and at Z = Z_sun and 0.1 Z_sun."""
+    g = golden("fine_structure_lines.txt")
+    h, c, kB = C["h"], C["c"], C["k_B"]
+    n = 1e10
+    for Z in (1.0, 0.1):
+        cfg = oracle.default_config(process_mask=oracle.P_L13_LINE, reaction_mask=0)
+        cfg.Z = Z
+        for T in (30.0, 100.0, 1000.0):
+            u = np.array([0.3, 1e-6, T, 20.0, 1e4 * C["a_rad"] * 20.0 ** 4])
+            A, b, F, M, ts, aux = oracle.system(n, u, 0.0, 0.0, 0.0, 1.0, 1.0, cfg)
+            lte = 0.0
+            for ion in ("CII", "OI"):
+                hnu = h * c / (g[f"lambda_{ion}_um"] * 1e-4)
+                e = g[f"g_{ion}"] * np.exp(-hnu / (kB * T))
+                lte += g[f"x_{ion}"] * Z * n * hnu * g[f"A_{ion}"] * e / (1.0 + e)
+            assert -aux[4] == pytest.approx(lte, rel=2e-2, abs=0), (Z, T, -aux[4] / lte)
