@@ -76,6 +76,7 @@ MUTATIONS = [
     ("[O I] A x10", "A_O = 8.9e-5,", "A_O = 8.9e-4,"),
     ("[O I] statistical weight ratio 3/5 -> 5/3", "g_O = 0.6,", "g_O = 1.6667,"),
     ("[C II] abundance x10", "const double x_C = 1.4e-4,", "const double x_C = 1.4e-3,"),
+    ("k_H9 cross-section x10 (stand-in R19)", "const double sigma_EUV = 6.3e-18;", "const double sigma_EUV = 6.3e-17;"),
     # other printed rates
     ("k_H0 slope 13.536556 -> 13.636556", "-32.71396786, 13.536556,", "-32.71396786, 13.636556,"),
     ("k_H1 x10", "k[1] = 2.753e-14", "k[1] = 2.753e-13"),

@@ -465,3 +465,16 @@ def test_line_cooling_stand_in_at_lte():
                 e = g[f"g_{ion}"] * np.exp(-hnu / (kB * T))
                 lte += g[f"x_{ion}"] * Z * n * hnu * g[f"A_{ion}"] * e / (1.0 + e)
             assert -aux[4] == pytest.approx(lte, rel=2e-2, abs=0), (Z, T, -aux[4] / lte)
+
+
+def test_k_H9_cross_section_is_the_hydrogenic_threshold_value():
+    """Reading R19 (stand-in for the cited photoionization rate): k_H9 =
+    c sigma n_EUV with sigma the photoionization cross-section of H(1s) at
+    threshold, which for a hydrogenic ground state is
+    sigma_0 = (2^9 pi^2 / (3 e^4)) alpha a_0^2 = 6.30e-18 cm^2 (e = exp(1);
+    Bethe & Salpeter's closed form, CODATA alpha and a_0), to the 3 digits the
+    stand-in carries.  Catches a wrong cross-section or a missing c."""
+    sigma0 = 2.0 ** 9 * np.pi ** 2 / (3.0 * np.e ** 4) * C["alpha_fs"] * C["a0_cm"] ** 2
+    for n_euv in (1e-3, 1.0):
+        k9 = oracle.rates(1e4, 20.0, 1.0, 0.0, n_euv, 0.0)[9]
+        assert k9 / (C["c"] * n_euv) == pytest.approx(sigma0, rel=1e-3, abs=0)
