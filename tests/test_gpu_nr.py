@@ -8,9 +8,10 @@ a large step converging to another root of the backward-Euler equations
 (the cold and the warm branch of a thermally unstable cell).  Each cell's
 path is known on both sides (accepted substeps, status bits and outer T_gas
 iterations, n_itr), so: a cell on the oracle's path agrees within the
-method's tolerance, 1e-4 relative (measured: up to 2.5e-5); cells on another
-path are a minority (at most 10 per cent); every cell is a valid state
-(finite, conserved, within bounds)."""
+method's tolerance, 1e-4 relative (measured: up to 2.5e-5), and within 1e-9
+for the short 10-yr step (measured 1.1e-11); cells on another path are a
+minority (measured 1.5 % at 10 yr and 7.0 % at 1e3 yr; bars 3 % and 8 %);
+every cell is a valid state (finite, conserved, within bounds)."""
 import numpy as np
 import pytest
 
@@ -35,8 +36,14 @@ def run_nr(cells, dt, cd):
     return out
 
 
-@pytest.mark.parametrize("dt_yr,cd,seed", [(10.0, 1.0, 3), (1e3, 1.0, 1001), (1e3, 1000.0, 1001)])
-def test_nr_matches_oracle_per_path(dt_yr, cd, seed):
+# per case: the smallest share of cells on the oracle's path and the largest
+# score on them (score 1 = 1e-9 relative), from the measurement with a margin:
+# 10 yr: 98.5 % of the cells, score 1.1e-2; 1e3 yr: 93.0 %, score 2.5e4
+# (2.5e-5 relative, inside the method's 1e-4 convergence tolerance)
+@pytest.mark.parametrize("dt_yr,cd,seed,min_same,max_score", [(10.0, 1.0, 3, 0.97, 1.0),
+                                                              (1e3, 1.0, 1001, 0.92, 1e5),
+                                                              (1e3, 1000.0, 1001, 0.92, 1e5)])
+def test_nr_matches_oracle_per_path(dt_yr, cd, seed, min_same, max_score):
     cells = inputs.cells_uniform(2048, seed=seed)
     ref = oracle.nr_step(cells, dt_yr * YR, cd)
     got = run_nr(cells, dt_yr * YR, cd)
@@ -47,8 +54,8 @@ def test_nr_matches_oracle_per_path(dt_yr, cd, seed):
     assert st["newton_iters"] == int(got["n_itr"].astype(np.int64).sum())
     print(f"same-path cells {same.sum()} of {same.size}; score max there {e[same].max():.2e}, "
           f"elsewhere {e[~same].max() if (~same).any() else 0:.2e} (score 1 = 1e-9 relative)")
-    assert np.all(e[same] <= 1e5)                # 1e-4 relative: the method's convergence tolerance
-    assert same.mean() >= 0.9
+    assert np.all(e[same] <= max_score)
+    assert same.mean() >= min_same
     for k in ("T_g", "T_d", "E_IR", "y_H2", "y_e", "y_H"):
         assert np.all(np.isfinite(got[k])), k
     assert np.all((got["y_H"] >= 0) & (got["y_H2"] >= 0) & (got["y_e"] >= 0) & (got["y_e"] <= 1))
